@@ -1,0 +1,147 @@
+/*
+ * hts.h -- C ABI of the GB300 (sm_103a) library for the two-stage reduction of a real
+ * matrix pencil (A, B) to Hessenberg-triangular (HT) form, after Steel & Vandebril,
+ * "Parallel two-stage reduction to Hessenberg-triangular form".
+ *
+ * The decomposition (Section 1 of the paper): orthogonal Q, Z, upper Hessenberg H and upper
+ * triangular T with (A, B) = Q (H, T) Z^T.  A pencil is in r-Hessenberg-triangular (r-HT)
+ * form when T is upper triangular and H(i, j) = 0 for i > j + r.
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are device pointers to column-major FP64 arrays owned by the caller; the
+ *    leading dimension must be >= max(1, n).  The library never allocates device memory on
+ *    these paths: all scratch lives in the caller's `work` buffer, whose size
+ *    hts_workspace_size() reports.  `work` must be 256-byte aligned.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy
+ *    default stream).  Argument errors are detected on the host before anything is
+ *    enqueued and are returned as HTS_ERR_ARG / HTS_ERR_WORKSPACE / HTS_ERR_UNSUPPORTED.
+ *    Errors found on the device (a bounded inter-block wait that ran out) are recorded in a
+ *    status word of the context and reported by hts_sync_status().
+ *  - On exit A holds H and B holds T with exact zeros below the first subdiagonal of H and
+ *    below the diagonal of T.
+ *  - compq / compz: HTS_COMP_NONE leaves Q / Z untouched (the pointer may be NULL);
+ *    HTS_COMP_INIT overwrites it with the stage's own orthogonal factor; HTS_COMP_UPDATE
+ *    multiplies it from the right (Q := Q Q_stage), so that A_in = Q H Z^T holds for the
+ *    matrices passed in.
+ */
+#ifndef HTS_H
+#define HTS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HTS_OK = 0,
+    HTS_ERR_ARG = 1,          /* invalid size, leading dimension, pointer or parameter */
+    HTS_ERR_CUDA = 2,         /* a CUDA runtime call failed (launch, stream, device) */
+    HTS_ERR_WORKSPACE = 3,    /* work is NULL, misaligned or smaller than required */
+    HTS_ERR_TIMEOUT = 4,      /* a bounded wait between thread blocks ran out (device) */
+    HTS_ERR_NONFINITE = 5,    /* reserved: NaN / Inf input */
+    HTS_ERR_UNSUPPORTED = 6   /* valid request this build does not implement */
+} hts_status;
+
+typedef enum {
+    HTS_COMP_NONE = 0,
+    HTS_COMP_INIT = 1,
+    HTS_COMP_UPDATE = 2
+} hts_comp;
+
+/* Arithmetic of the delayed reflector-block updates (the far-from-diagonal updates of
+ * Alg. 4 of the paper).  The near-diagonal chase always runs in native FP64. */
+typedef enum {
+    HTS_GEMM_FP64 = 0,        /* native FP64 */
+    HTS_GEMM_EMU_BF16 = 1     /* FP64 emulated on BF16 tensor cores (split operands) */
+} hts_gemm_mode;
+
+/* Tuning parameters; 0 selects the library default.
+ *  q          sweeps grouped per generate/apply iteration (Section "Blocked stage two");
+ *             1 <= q <= r.  Default: r.
+ *  p          stage-1 block height in units of r (Alg. 1); p >= 2.  Default: 8.
+ *  emu_slices number of BF16 slices per FP64 operand in HTS_GEMM_EMU_BF16 mode.
+ *  tile_m, tile_n  reserved.
+ *  flags      bit 0 (HTS_FLAG_NO_CLEAN): skip the final exact zeroing below the band.
+ *             bit 30 (HTS_FLAG_TEST_STALL): fault injection for tests of the failure path:
+ *             the chase block of the first sweep never publishes its progress, so the next
+ *             block's bounded wait (2 s) runs out and HTS_ERR_TIMEOUT is reported by
+ *             hts_sync_status; every later kernel of the call then returns at once. */
+typedef struct {
+    int q;
+    int p;
+    int emu_slices;
+    int tile_m;
+    int tile_n;
+    int flags;
+} hts_params;
+
+#define HTS_FLAG_NO_CLEAN 1
+#define HTS_FLAG_TEST_STALL (1 << 30)
+
+typedef struct hts_ctx hts_ctx;
+
+/* Create a context bound to CUDA device `device` (allocates a small device status word).
+ * Returns HTS_ERR_ARG for a NULL ctx pointer, HTS_ERR_CUDA if the device is unusable. */
+hts_status hts_create(hts_ctx **ctx, int device);
+
+/* Destroy a context created by hts_create (NULL is ignored). */
+void hts_destroy(hts_ctx *ctx);
+
+/* Bytes of `work` needed by hts_reduce_stage1 / hts_reduce_stage2 / hts_reduce for an n x n
+ * pencil with r subdiagonals and parameters p (NULL = defaults).  The size covers all three
+ * entry points. */
+hts_status hts_workspace_size(int n, int r, const hts_params *p, size_t *bytes);
+
+/*
+ * Stage 1: Alg. 1 of the paper ("Blocked stage 1").  Requires B upper triangular (its
+ * strictly lower part is ignored and zeroed) and 1 <= r < n.  On exit (A, B) is in r-HT form.
+ */
+hts_status hts_reduce_stage1(hts_ctx *ctx, int n, int r,
+                             double *A, int lda, double *B, int ldb,
+                             hts_comp compq, double *Q, int ldq,
+                             hts_comp compz, double *Z, int ldz,
+                             hts_gemm_mode mode, const hts_params *p,
+                             void *work, size_t work_bytes, void *stream);
+
+/*
+ * Stage 2: reduction of an r-HT pencil to HT form by bulge chasing (Section "Reduction to
+ * Hessenberg-triangular form"; Alg. 2 defines the reflectors, Alg. 3 and Alg. 4 the blocked
+ * generate / apply schedule this implementation runs).  Requires 1 <= r and n >= 1; entries
+ * of A below the r-th subdiagonal and of B below the diagonal are treated as zero.  r = 1
+ * (and n <= 2) is a no-op apart from HTS_COMP_INIT.  Reflectors act on rows/columns 2..n
+ * only, so Q e_1 and Z e_1 are unchanged.
+ */
+hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r,
+                             double *A, int lda, double *B, int ldb,
+                             hts_comp compq, double *Q, int ldq,
+                             hts_comp compz, double *Z, int ldz,
+                             hts_gemm_mode mode, const hts_params *p,
+                             void *work, size_t work_bytes, void *stream);
+
+/*
+ * Full reduction of a dense pencil: QR of B (stage 0; the paper QR-factorises B first,
+ * Section "Experiments"), then stage 1 with n_b = r, then stage 2.  Requires 1 <= r < n.
+ */
+hts_status hts_reduce(hts_ctx *ctx, int n, int r,
+                      double *A, int lda, double *B, int ldb,
+                      hts_comp compq, double *Q, int ldq,
+                      hts_comp compz, double *Z, int ldz,
+                      hts_gemm_mode mode, const hts_params *p,
+                      void *work, size_t work_bytes, void *stream);
+
+/*
+ * Wait for `stream`, then report and clear the context's device status word.
+ * info (may be NULL) receives {pencil, group, k, j} of the first device-side error.
+ * Returns HTS_OK, HTS_ERR_TIMEOUT, or HTS_ERR_CUDA if the stream itself failed.
+ */
+hts_status hts_sync_status(hts_ctx *ctx, void *stream, int info[4]);
+
+/* Human-readable name of a status code (static string). */
+const char *hts_status_string(hts_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HTS_H */

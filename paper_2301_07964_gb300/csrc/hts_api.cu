@@ -1,0 +1,245 @@
+// C-ABI entry points of the HT-reduction library (declared in include/hts.h).
+#include <cstdlib>
+#include <cstring>
+
+#include "hts_internal.cuh"
+
+namespace hts {
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard()
+    {
+        if (ok && prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Workspace layout of stage 2 (reflectors of one group, progress words).
+struct S2Layout {
+    int kdim, qmax;
+    size_t off_vq, off_tq, off_vz, off_tz, off_flags, total;
+};
+
+S2Layout s2_layout(int n, int r)
+{
+    S2Layout L;
+    L.kdim = 2 + n / (r > 0 ? r : 1);
+    L.qmax = r;
+    const size_t nv = (size_t)L.qmax * L.kdim * r * sizeof(double);
+    const size_t nt = (size_t)L.qmax * L.kdim * sizeof(double);
+    size_t o = 0;
+    L.off_vq = o; o = align_up(o + nv, 256);
+    L.off_tq = o; o = align_up(o + nt, 256);
+    L.off_vz = o; o = align_up(o + nv, 256);
+    L.off_tz = o; o = align_up(o + nt, 256);
+    L.off_flags = o; o = align_up(o + (size_t)L.qmax * sizeof(unsigned long long), 256);
+    L.total = o;
+    return L;
+}
+
+bool bad_matrix(const double *M, int ld, int n) { return M == nullptr || ld < (n > 1 ? n : 1); }
+
+hts_status check_common(hts_ctx *ctx, int n, int r, const double *A, int lda, const double *B, int ldb,
+                        hts_comp compq, const double *Q, int ldq, hts_comp compz, const double *Z, int ldz,
+                        hts_gemm_mode mode)
+{
+    if (!ctx || n < 0 || r < 1) return HTS_ERR_ARG;
+    if (n == 0) return HTS_OK;
+    if (bad_matrix(A, lda, n) || bad_matrix(B, ldb, n)) return HTS_ERR_ARG;
+    if (compq < HTS_COMP_NONE || compq > HTS_COMP_UPDATE) return HTS_ERR_ARG;
+    if (compz < HTS_COMP_NONE || compz > HTS_COMP_UPDATE) return HTS_ERR_ARG;
+    if (compq != HTS_COMP_NONE && bad_matrix(Q, ldq, n)) return HTS_ERR_ARG;
+    if (compz != HTS_COMP_NONE && bad_matrix(Z, ldz, n)) return HTS_ERR_ARG;
+    if (mode != HTS_GEMM_FP64 && mode != HTS_GEMM_EMU_BF16) return HTS_ERR_ARG;
+    return HTS_OK;
+}
+
+hts_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HTS_OK : HTS_ERR_CUDA; }
+
+}  // namespace
+
+// Stage 2 driver: the group loop of generate / apply launches.
+hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B, int ldb,
+                      double *Q, int ldq, double *Z, int ldz, int q, int flags,
+                      void *work, cudaStream_t st)
+{
+    if (n <= 2 || r <= 1) return HTS_OK;
+    const S2Layout L = s2_layout(n, r);
+    char *w = static_cast<char *>(work);
+    ReflectorSet R;
+    R.VQ = reinterpret_cast<double *>(w + L.off_vq);
+    R.TQ = reinterpret_cast<double *>(w + L.off_tq);
+    R.VZ = reinterpret_cast<double *>(w + L.off_vz);
+    R.TZ = reinterpret_cast<double *>(w + L.off_tz);
+    R.kdim = L.kdim;
+    unsigned long long *fl = reinterpret_cast<unsigned long long *>(w + L.off_flags);
+    cudaError_t e = cudaMemsetAsync(fl, 0, (size_t)L.qmax * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return HTS_ERR_CUDA;
+
+    int group = 0;
+    for (int j1 = 1; j1 <= n - 2; j1 += q, ++group) {
+        const int qg = imin(q, n - 2 - j1 + 1);
+        GenArgs ga;
+        ga.A = A; ga.B = B; ga.lda = lda; ga.ldb = ldb;
+        ga.n = n; ga.r = r; ga.j1 = j1; ga.qg = qg; ga.group = group;
+        ga.R = R; ga.flags = fl;
+        ga.epoch = (unsigned long long)(group + 1) << 32;
+        ga.status = ctx->d_status;
+        ga.stall = (flags & HTS_FLAG_TEST_STALL) ? 1 : 0;
+        if ((e = launch_s2_generate(ga, st)) != cudaSuccess) return HTS_ERR_CUDA;
+
+        ApplyArgs aa;
+        int nm = 0;
+        aa.M[nm] = A; aa.ld[nm] = lda; aa.kind[nm] = 0; ++nm;
+        aa.M[nm] = B; aa.ld[nm] = ldb; aa.kind[nm] = 1; ++nm;
+        if (Z) { aa.M[nm] = Z; aa.ld[nm] = ldz; aa.kind[nm] = 2; ++nm; }
+        if (Q) { aa.M[nm] = Q; aa.ld[nm] = ldq; aa.kind[nm] = 3; ++nm; }
+        for (int i = nm; i < 4; ++i) { aa.M[i] = nullptr; aa.ld[i] = 1; aa.kind[i] = 0; }
+        aa.n = n; aa.r = r; aa.j1 = j1; aa.qg = qg; aa.R = R; aa.status = ctx->d_status;
+        if ((e = launch_s2_apply_right(aa, nm, st)) != cudaSuccess) return HTS_ERR_CUDA;
+
+        LeftArgs la;
+        la.A = A; la.B = B; la.lda = lda; la.ldb = ldb;
+        la.n = n; la.r = r; la.j1 = j1; la.qg = qg; la.R = R; la.status = ctx->d_status;
+        if ((e = launch_s2_apply_left(la, st)) != cudaSuccess) return HTS_ERR_CUDA;
+    }
+    if (!(flags & HTS_FLAG_NO_CLEAN)) {
+        if ((e = launch_zero_below(A, lda, n, 1, st)) != cudaSuccess) return HTS_ERR_CUDA;
+        if ((e = launch_zero_below(B, ldb, n, 0, st)) != cudaSuccess) return HTS_ERR_CUDA;
+    }
+    return HTS_OK;
+}
+
+}  // namespace hts
+
+using namespace hts;
+
+extern "C" {
+
+const char *hts_status_string(hts_status s)
+{
+    switch (s) {
+    case HTS_OK: return "HTS_OK";
+    case HTS_ERR_ARG: return "HTS_ERR_ARG";
+    case HTS_ERR_CUDA: return "HTS_ERR_CUDA";
+    case HTS_ERR_WORKSPACE: return "HTS_ERR_WORKSPACE";
+    case HTS_ERR_TIMEOUT: return "HTS_ERR_TIMEOUT";
+    case HTS_ERR_NONFINITE: return "HTS_ERR_NONFINITE";
+    case HTS_ERR_UNSUPPORTED: return "HTS_ERR_UNSUPPORTED";
+    }
+    return "unknown hts_status";
+}
+
+hts_status hts_create(hts_ctx **ctx, int device)
+{
+    if (!ctx) return HTS_ERR_ARG;
+    *ctx = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return HTS_ERR_CUDA;
+    DeviceGuard g(device);
+    if (!g.ok) return HTS_ERR_CUDA;
+    hts_ctx *c = static_cast<hts_ctx *>(std::calloc(1, sizeof(hts_ctx)));
+    if (!c) return HTS_ERR_CUDA;
+    c->device = device;
+    if (cudaMalloc(&c->d_status, kStatusWords * sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->d_status, 0, kStatusWords * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->h_status, kStatusWords * sizeof(int)) != cudaSuccess) {
+        if (c->d_status) cudaFree(c->d_status);
+        std::free(c);
+        return HTS_ERR_CUDA;
+    }
+    *ctx = c;
+    return HTS_OK;
+}
+
+void hts_destroy(hts_ctx *ctx)
+{
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    std::free(ctx);
+}
+
+hts_status hts_workspace_size(int n, int r, const hts_params *p, size_t *bytes)
+{
+    (void)p;
+    if (!bytes || n < 0 || r < 1) return HTS_ERR_ARG;
+    *bytes = s2_layout(n, r).total;
+    return HTS_OK;
+}
+
+hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B, int ldb,
+                             hts_comp compq, double *Q, int ldq, hts_comp compz, double *Z, int ldz,
+                             hts_gemm_mode mode, const hts_params *p, void *work, size_t work_bytes,
+                             void *stream)
+{
+    hts_status s = check_common(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode);
+    if (s != HTS_OK || n == 0) return s;
+    if (r > kMaxR) return HTS_ERR_UNSUPPORTED;
+    if (mode != HTS_GEMM_FP64) return HTS_ERR_UNSUPPORTED;
+    int q = (p && p->q > 0) ? p->q : r;
+    if (q > r) return HTS_ERR_ARG;
+    const int flags = p ? p->flags : 0;
+    const bool needs_work = n > 2 && r > 1;
+    if (needs_work) {
+        if (!work || (reinterpret_cast<uintptr_t>(work) & 255u)) return HTS_ERR_WORKSPACE;
+        if (work_bytes < s2_layout(n, r).total) return HTS_ERR_WORKSPACE;
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return HTS_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double *Qp = compq == HTS_COMP_NONE ? nullptr : Q;
+    double *Zp = compz == HTS_COMP_NONE ? nullptr : Z;
+    if (compq == HTS_COMP_INIT && (s = cuda_status(launch_set_identity(Q, ldq, n, st))) != HTS_OK) return s;
+    if (compz == HTS_COMP_INIT && (s = cuda_status(launch_set_identity(Z, ldz, n, st))) != HTS_OK) return s;
+    return run_stage2(ctx, n, r, A, lda, B, ldb, Qp, ldq, Zp, ldz, q, flags, work, st);
+}
+
+hts_status hts_reduce_stage1(hts_ctx *ctx, int n, int r, double *A, int lda, double *B, int ldb,
+                             hts_comp compq, double *Q, int ldq, hts_comp compz, double *Z, int ldz,
+                             hts_gemm_mode mode, const hts_params *p, void *work, size_t work_bytes,
+                             void *stream)
+{
+    (void)p; (void)work; (void)work_bytes; (void)stream;
+    hts_status s = check_common(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode);
+    if (s != HTS_OK || n == 0) return s;
+    return HTS_ERR_UNSUPPORTED;
+}
+
+hts_status hts_reduce(hts_ctx *ctx, int n, int r, double *A, int lda, double *B, int ldb,
+                      hts_comp compq, double *Q, int ldq, hts_comp compz, double *Z, int ldz,
+                      hts_gemm_mode mode, const hts_params *p, void *work, size_t work_bytes, void *stream)
+{
+    (void)p; (void)work; (void)work_bytes; (void)stream;
+    hts_status s = check_common(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode);
+    if (s != HTS_OK || n == 0) return s;
+    return HTS_ERR_UNSUPPORTED;
+}
+
+hts_status hts_sync_status(hts_ctx *ctx, void *stream, int info[4])
+{
+    if (!ctx) return HTS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return HTS_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HTS_ERR_CUDA;
+    if (cudaMemcpy(ctx->h_status, ctx->d_status, kStatusWords * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HTS_ERR_CUDA;
+    if (cudaMemset(ctx->d_status, 0, kStatusWords * sizeof(int)) != cudaSuccess) return HTS_ERR_CUDA;
+    if (info)
+        for (int i = 0; i < 4; ++i) info[i] = ctx->h_status[1 + i];
+    return static_cast<hts_status>(ctx->h_status[0]);
+}
+
+}  // extern "C"

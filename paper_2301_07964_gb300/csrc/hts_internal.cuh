@@ -1,0 +1,193 @@
+// Internal definitions shared by the stage-2 kernels and the C-ABI layer.
+//
+// Index convention: the paper's 1-based (row, column) indices are used throughout the
+// scheduling code; AT() converts to a column-major offset.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hts.h"
+
+struct hts_ctx {
+    int device;
+    int *d_status;   // device status word: [0] code, [1..4] {pencil, group, k, j}
+    int *h_status;   // pinned host mirror used by hts_sync_status
+};
+
+namespace hts {
+
+constexpr int kStatusWords = 8;
+constexpr int kMaxR = 32;            // reflector length limit of the warp-level chase
+constexpr int kGenThreads = 256;     // threads of one generate (chase) block
+constexpr int kApplyThreads = 128;   // threads (rows or columns) of one apply block
+constexpr long long kSpinLimit = 1LL << 24;   // bounded waits: polls before giving up
+constexpr unsigned long long kWaitLimitNs = 2000000000ULL;   // ... or 2 s of wall clock
+
+__host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
+
+__host__ __device__ __forceinline__ size_t AT(int ld, int i, int j)
+{
+    return (size_t)(i - 1) + (size_t)(j - 1) * (size_t)ld;
+}
+
+// Number of blocks of sweep j that carry reflectors (Alg. 2: 1 + floor((n-j-2)/r)).
+__host__ __device__ __forceinline__ int nblocks_gen(int n, int r, int j)
+{
+    return (n - j - 2 >= 0) ? 1 + (n - j - 2) / r : 0;
+}
+
+// Number of blocks of sweep j visited by the generate phase (Alg. 3: 2 + floor((n-j-1)/r)).
+// The blocks beyond nblocks_gen only receive the lazy left updates of their pivot column.
+__host__ __device__ __forceinline__ int nblocks_lazy(int n, int r, int j)
+{
+    return 2 + (n - j - 1) / r;
+}
+
+// Index ranges of step (k, j) inside the group that starts at sweep j1 and has qg sweeps.
+//  jb: pivot column; i1..i2: rows of the left reflector and columns of the right one;
+//  i3: last row of A the right reflector touches (Alg. 2); i4: first row of the band that
+//  the generate phase updates.  i4 follows the row-range derivation of the text
+//  (j1 + 1 + max(0, (k + j - j1 - q) r)); Alg. 3 prints a value 2r larger, which leaves
+//  rows of the B block without the preceding right reflector when its RQ is formed.
+struct StepGeom {
+    int jb, i1, i2, i3, i4;
+};
+
+__host__ __device__ __forceinline__ StepGeom step_geom(int n, int r, int j1, int qg, int k, int j)
+{
+    StepGeom g;
+    g.jb = j + imax(0, (k - 1) * r + 1);
+    g.i1 = j + k * r + 1;
+    g.i2 = imin(j + (k + 1) * r, n);
+    g.i3 = imin(j + (k + 2) * r, n);
+    g.i4 = j1 + 1 + imax(0, (k + j - j1 - qg) * r);
+    return g;
+}
+
+// Reflector storage for one group: slot s = j - j1, block k.
+//   V[(s * kdim + k) * r + i], i < r (v[0] = 1 stored explicitly, zero padded)
+//   T[s * kdim + k]            (tau = 0: no reflector / identity)
+struct ReflectorSet {
+    double *VQ, *TQ, *VZ, *TZ;
+    int kdim;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Record the first device-side error; later errors are dropped.
+__device__ __forceinline__ void record_error(int *status, int code, int a, int b, int c, int d)
+{
+    if (atomicCAS(status, 0, code) == 0) {
+        status[1] = a;
+        status[2] = b;
+        status[3] = c;
+        status[4] = d;
+        __threadfence();
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Householder reflector in the LAPACK dlarfg convention, computed by one full warp.
+// Lane i holds x_i for i < m (x_0 = alpha), garbage-free zero elsewhere.  Returns tau and
+// sets *beta and v_i (v_0 = 1) in the calling lane's register.  tau = 0 when x_2..x_m = 0.
+// The sum of squares is formed directly and recomputed with scaling only when it
+// over- or underflows.
+__device__ __forceinline__ double warp_larfg(double xi, int m, int lane, double *beta, double *vi)
+{
+    double alpha = __shfl_sync(0xffffffffu, xi, 0);
+    double t = (lane >= 1 && lane < m) ? xi : 0.0;
+    double ssq = warp_sum(t * t);
+    double xnorm2 = ssq;
+    double scale = 1.0;
+    if (!(ssq >= 1e-290 && ssq <= 1e290) || fabs(alpha) > 1e145) {
+        double mx = warp_max(fabs(t));
+        mx = fmax(mx, fabs(alpha));
+        if (mx == 0.0) {
+            *beta = alpha;
+            *vi = (lane == 0) ? 1.0 : 0.0;
+            return 0.0;
+        }
+        scale = mx;
+        double ts = t / mx;
+        xnorm2 = warp_sum(ts * ts);
+    }
+    if (xnorm2 == 0.0) {
+        *beta = alpha;
+        *vi = (lane == 0) ? 1.0 : 0.0;
+        return 0.0;
+    }
+    double as = alpha / scale;
+    double nrm = scale * sqrt(as * as + xnorm2);
+    double b = (alpha >= 0.0) ? -nrm : nrm;
+    double tau = (b - alpha) / b;
+    double sc = 1.0 / (alpha - b);
+    *beta = b;
+    *vi = (lane == 0) ? 1.0 : ((lane < m) ? xi * sc : 0.0);
+    return tau;
+}
+
+// Arguments of the stage-2 launches (kernels in stage2.cu).
+struct GenArgs {
+    double *A;
+    double *B;
+    int lda, ldb;
+    int n, r, j1, qg, group;
+    ReflectorSet R;
+    unsigned long long *flags;   // one progress word per sweep slot
+    unsigned long long epoch;    // (group + 1) << 32
+    int *status;
+    int stall;                   // fault injection: slot 0 never publishes (tests only)
+};
+
+// kind 0 = A, 1 = B (Z^ reflectors on rows x < i4(k, j)), 2 = Z (Z^, all rows),
+// 3 = Q (Q^, all rows)
+struct ApplyArgs {
+    double *M[4];
+    int ld[4];
+    int kind[4];
+    int n, r, j1, qg;
+    ReflectorSet R;
+    const int *status;
+};
+
+struct LeftArgs {
+    double *A;
+    double *B;
+    int lda, ldb;
+    int n, r, j1, qg;
+    ReflectorSet R;
+    const int *status;
+};
+
+cudaError_t launch_s2_generate(const GenArgs &a, cudaStream_t st);
+cudaError_t launch_s2_apply_right(const ApplyArgs &a, int nmat, cudaStream_t st);
+cudaError_t launch_s2_apply_left(const LeftArgs &a, cudaStream_t st);
+cudaError_t launch_set_identity(double *M, int ld, int n, cudaStream_t st);
+cudaError_t launch_zero_below(double *M, int ld, int n, int band, cudaStream_t st);
+
+}  // namespace hts
