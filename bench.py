@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of stage 2 of the two-stage Hessenberg-triangular reduction on GB300.
+
+Metric: stage-2 GFLOP/s, FP64-equivalent with the paper's operation count for stage 2
+(10 n^3 including Q and Z), plus the backward error, on one n = 8192, r = 16 pencil.
+
+One step = one full stage-2 reduction (all sweeps, all kernels) of a seeded synthetic
+r-Hessenberg-triangular pencil (A with 16 subdiagonals, B the R factor of a Gaussian matrix),
+with Q and Z accumulated.  The inputs (1 GiB for A and B) are larger than L2, and each step
+restores A and B from pristine device copies before the timed call.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mode fp64|emu]
+
+``--impl reference`` times the CPU oracle (Alg. 2 in plain C, OpenMP) on the host cores:
+each step is a bounded sample (the first sweeps) of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "stage-2 GFLOP/s (FP64-equiv) + backward error at n=8192,r=16 on 1 GB300"
+UNIT = "GFLOP/s"
+N_DEFAULT, R_DEFAULT, SEED = 8192, 16, 4
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+KERNEL_SOURCES = {"k_s2_generate": "stage2.cu", "k_s2_apply_right": "stage2.cu",
+                  "k_s2_apply_left": "stage2.cu"}
+
+
+def paper_flops(n):
+    """Paper's stage-2 operation count with Q and Z: 10 n^3 (Section "Unblocked stage two")."""
+    return 10.0 * float(n) ** 3
+
+
+def sweep_work(n, r):
+    """Direct flop count of each sweep of Alg. 2 (4 flops per element and reflector), used to
+    scale a bounded oracle sample to its share of the whole stage."""
+    w = np.zeros(n + 1)
+    for j in range(1, n - 1):
+        nb = 1 + (n - j - 2) // r
+        k = np.arange(nb)
+        jb = j + np.maximum(0, (k - 1) * r + 1)
+        i1 = j + k * r + 1
+        i2 = np.minimum(j + (k + 1) * r, n)
+        i3 = np.minimum(j + (k + 2) * r, n)
+        m = i2 - i1 + 1
+        w[j] = float(np.sum(4 * m * ((n - jb) + (n - i1 + 1) + n + i3 + i2 + n)))
+    return w
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(self.NAMES, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------------------
+def log(msg):
+    sys.stderr.write("[bench] %s\n" % msg)
+    sys.stderr.flush()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def source_digest(fname):
+    path = os.path.join(ROOT, "paper_2301_07964_gb300", "csrc", fname)
+    h = hashlib.sha256()
+    for p in sorted([path, os.path.join(ROOT, "paper_2301_07964_gb300", "csrc", "hts_internal.cuh")]):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, or None when the summary is
+    missing or was taken on a different version of the kernel's source."""
+    try:
+        lines = open(TRAFFIC_FILE).read().splitlines()
+    except OSError:
+        return None
+    digest = source_digest(KERNEL_SOURCES.get(kernel, "stage2.cu"))
+    for ln in lines:
+        parts = ln.split()
+        if len(parts) >= 4 and not ln.startswith("#") and parts[0] == kernel and parts[1] == workload:
+            if parts[3] == digest:
+                return float(parts[2])
+    return None
+
+
+def cpu_sample(A, B, r, budget_s):
+    """Time the oracle on the first sweeps of stage 2 (bounded sample).  Returns
+    (GFLOP/s in the paper's convention, seconds, sweeps, share of the stage, threads)."""
+    import oracle
+    n = A.shape[0]
+    w = sweep_work(n, r)
+    total = w.sum()
+    hs_of = lambda s: int(sum(2 * (1 + (n - j - 2) // r) for j in range(1, s + 1)))
+    t0 = time.perf_counter()
+    oracle.stage2(A, B, r, max_half_steps=hs_of(2))
+    t_cal = max(time.perf_counter() - t0, 1e-3)
+    s = int(max(2, min(n - 2, 2 * budget_s / t_cal)))
+    t0 = time.perf_counter()
+    oracle.stage2(A, B, r, max_half_steps=hs_of(s))
+    t = time.perf_counter() - t0
+    share = float(w[1:s + 1].sum() / total)
+    return paper_flops(n) * share / t / 1e9, t, s, share, oracle.threads()
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------------------
+def run_reference(args, n, r):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2301_07964_gb300.inputs import random_rht_pencil
+    oracle.build()
+    A, B = random_rht_pencil(n, r, SEED)
+    w = sweep_work(n, r)
+    total = w.sum()
+    s = int(args.ref_sweeps)
+    hs = int(sum(2 * (1 + (n - j - 2) // r) for j in range(1, s + 1)))
+    share = float(w[1:s + 1].sum() / total)
+    for _ in range(args.warmup):
+        oracle.stage2(A, B, r, max_half_steps=hs)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.stage2(A, B, r, max_half_steps=hs)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = paper_flops(n) * share / t / 1e9
+    sample = ("first %d of %d sweeps of the n=%d r=%d pencil (%.2f%% of stage-2 work), Q and Z "
+              "accumulated, scaled by that share" % (s, n - 2, n, r, 100 * share))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "stage 2, n=%d r=%d, seeded r-HT pencil, Q and Z accumulated" % (n, r),
+                   "n": n, "r": r},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def run_ours(args, n, r):
+    import torch
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2301_07964_gb300 import binding as b
+    from paper_2301_07964_gb300 import build
+    from paper_2301_07964_gb300.device import Reducer, colmajor_empty, to_device
+    from paper_2301_07964_gb300.inputs import random_rht_pencil
+    if rank == 0 or not os.path.exists(build.LIB_PATH):
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    b.load()
+
+    q = args.q or r
+    mode = b.HTS_GEMM_FP64 if args.mode == "fp64" else b.HTS_GEMM_EMU_BF16
+    A, B = random_rht_pencil(n, r, SEED)
+    dA0, dB0 = to_device(A), to_device(B)
+    dA, dB = colmajor_empty(n), colmajor_empty(n)
+    dQ, dZ = colmajor_empty(n), colmajor_empty(n)
+    red = Reducer(local)
+    stream = torch.cuda.current_stream()
+    fp64_peak = b.hts_probe_fp64_peak(stream)
+
+    def one_step():
+        dA.copy_(dA0)
+        dB.copy_(dB0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, mode=mode,
+                   stream=stream)
+        e1.record(stream)
+        return e0, e1
+
+    for i in range(args.warmup):
+        e0, e1 = one_step()
+        torch.cuda.synchronize()
+        log("warm-up step %d: %.1f ms" % (i, e0.elapsed_time(e1)))
+    torch.cuda.synchronize()
+    st, info = red.sync_status()
+    if st != b.HTS_OK:
+        raise SystemExit("device error during warm-up: %s %s" % (b.status_string(st), info))
+
+    launches_per_step = 4 * ((n - 2 + q - 1) // q) + 4
+    b.hts_profile_begin(red.ctx, launches_per_step * args.steps + 16)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    events = [one_step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    prof, dropped = b.hts_profile_end(red.ctx)
+    st, info = red.sync_status()
+    if st != b.HTS_OK:
+        raise SystemExit("device error during timed steps: %s %s" % (b.status_string(st), info))
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in events]
+    ms = sum(step_ms) / len(step_ms)
+    log("timed steps (ms): %s; profile: %s" % (step_ms, json.dumps(prof)))
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # backward error of the last step (outside the timed region; residuals by cuBLAS DGEMM)
+    H, T, Qm, Zm = dA, dB, dQ, dZ
+    I = torch.eye(n, dtype=torch.float64, device="cuda")
+    bwd = {
+        "A": float(torch.linalg.norm(Qm @ H @ Zm.T - dA0) / torch.linalg.norm(dA0)),
+        "B": float(torch.linalg.norm(Qm @ T @ Zm.T - dB0) / torch.linalg.norm(dB0)),
+        "orth_Q": float(torch.linalg.norm(Qm.T @ Qm - I) / n ** 0.5),
+        "orth_Z": float(torch.linalg.norm(Zm.T @ Zm - I) / n ** 0.5),
+        "H_below_subdiag_max": float(torch.tril(H, -2).abs().max()),
+        "T_below_diag_max": float(torch.tril(T, -1).abs().max()),
+    }
+    del I
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory()   # row-major of A^T = col-major A
+        hB = torch.from_numpy(np.ascontiguousarray(B.T)).pin_memory()
+        outs = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(4)]
+        e2e_ms = []
+        for _ in range(max(1, args.e2e_steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dA.t().copy_(hA, non_blocking=True)
+            dB.t().copy_(hB, non_blocking=True)
+            red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, mode=mode,
+                       stream=stream)
+            for o, d in zip(outs, (dA, dB, dQ, dZ)):
+                o.copy_(d.t(), non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        st, info = red.sync_status()
+        if st != b.HTS_OK:
+            raise SystemExit("device error during e2e steps: %s %s" % (b.status_string(st), info))
+        e2e_t = sum(e2e_ms) / len(e2e_ms)
+        if dist is not None:
+            t = torch.tensor([e2e_t], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_t = float(t.item())
+        e2e = {"value": ws * paper_flops(n) / (e2e_t / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 4 * 8 * n * n,
+               "ms_per_step": e2e_t}
+
+    # roofline of the dominant kernel
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    kname, kp = dom
+    achieved = kp["flops"] / (kp["ms"] / 1e3) / 1e12
+    workload = "n%d_r%d_q%d_%s" % (n, r, q, args.mode)
+    traffic = ncu_traffic(kname, workload)
+    roofline = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "traffic": traffic,
+                "peak_source": "FP64 FMA throughput measured live by hts_probe_fp64_peak (of measured)",
+                "algorithmic_flops_per_launch": kp["flops"] / kp["launches"],
+                "algorithmic_bytes_per_launch": kp["bytes"] / kp["launches"],
+                "avg_launch_ms": kp["ms"] / kp["launches"]}
+    peaks = measured_peaks()
+    kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                   "share": v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values())),
+                   "tflops": v["flops"] / max(1e-9, v["ms"] / 1e3) / 1e12,
+                   "gbs": v["bytes"] / max(1e-9, v["ms"] / 1e3) / 1e9}
+               for k, v in prof.items()}
+
+    line = {
+        "metric": METRIC, "value": ws * paper_flops(n) / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "stage 2, n=%d r=%d q=%d, seeded r-HT pencil (A band iid N(0,1), B = R of "
+                               "a Gaussian), Q and Z accumulated, delayed updates %s" % (n, r, q, args.mode),
+                   "n": n, "r": r, "q": q, "mode": args.mode, "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs (A, B: %.1f GiB) larger than L2" % (2 * 8 * n * n / 2 ** 30)},
+        "backward_error": bwd,
+        "direct_gflops": ws * 8.0 * n ** 3 / (ms / 1e3) / 1e9,
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+        "profile_dropped": dropped,
+        "roofline": roofline,
+        "kernels": kernels,
+        "hbm_peak_gbs": peaks.get("hbm_gbs"),
+        "wall_s_timed": t_wall,
+    }
+    log(json.dumps(line))
+    if ws == 1 and rank == 0 and not args.no_cpu:
+        v, t, s, share, cores = cpu_sample(A, B, r, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "first %d of %d sweeps of the same pencil (%.2f%% of stage-2 work) "
+                                          "in %.1f s, Q and Z accumulated, scaled by that share" %
+                                          (s, n - 2, 100 * share, t)}
+    if rank == 0:
+        print(json.dumps(line))
+    red.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["fp64", "emu"], default="fp64")
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--r", type=int, default=R_DEFAULT)
+    ap.add_argument("--q", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-sweeps", type=int, default=24)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args, args.n, args.r)
+    return run_ours(args, args.n, args.r)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,52 @@
+/*
+ * hts_profile.h -- measurement utilities of the HT-reduction library.  These entry points
+ * have no counterpart in the paper: they exist so that a benchmark can time every kernel of a
+ * call with CUDA events on the stream the kernel runs on, and can measure the FP64
+ * arithmetic peak of the device it runs on.
+ */
+#ifndef HTS_PROFILE_H
+#define HTS_PROFILE_H
+
+#include "hts.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Kernel classes reported by the profiler. */
+enum {
+    HTS_K_GENERATE = 0,     /* near-diagonal chase (stage 2 generate phase) */
+    HTS_K_APPLY_RIGHT = 1,  /* delayed right updates of A, B, Z and Q (stage 2) */
+    HTS_K_APPLY_LEFT = 2,   /* delayed left updates of A and B (stage 2) */
+    HTS_K_UTIL = 3,         /* identity initialisation, final zeroing */
+    HTS_K_STAGE1 = 4,       /* stage 0 / stage 1 kernels */
+    HTS_K_NKINDS = 8
+};
+
+typedef struct {
+    int launches;      /* launches recorded */
+    double ms;         /* summed CUDA-event durations of those launches */
+    double flops;      /* algorithmic floating-point operations (4 per element and reflector) */
+    double bytes;      /* algorithmic DRAM bytes (each touched element read and written once) */
+} hts_kernel_profile;
+
+/* Start recording: preallocates 2 * max_launches CUDA events on the context's device (do
+ * this outside any timed region).  Subsequent calls on ctx record an event pair around every
+ * kernel launch until max_launches is reached.  HTS_ERR_ARG for bad arguments,
+ * HTS_ERR_CUDA if the events cannot be created. */
+hts_status hts_profile_begin(hts_ctx *ctx, int max_launches);
+
+/* Stop recording: waits for the last recorded event, sums the durations per kernel class
+ * into out[0 .. HTS_K_NKINDS-1] and releases the events.  *dropped (may be NULL) receives the
+ * number of launches that did not fit into the pool. */
+hts_status hts_profile_end(hts_ctx *ctx, hts_kernel_profile out[HTS_K_NKINDS], int *dropped);
+
+/* Measure the FP64 fused multiply-add throughput of the current device (TFLOP/s, 2 flops per
+ * FMA) with a short kernel on `stream`; blocks until it finishes. */
+hts_status hts_probe_fp64_peak(void *stream, double *tflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HTS_PROFILE_H */

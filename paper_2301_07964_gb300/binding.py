@@ -38,6 +38,15 @@ class hts_params(ctypes.Structure):
                 ("tile_m", ctypes.c_int), ("tile_n", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
+HTS_K_NKINDS = 8
+KERNEL_KINDS = {0: "k_s2_generate", 1: "k_s2_apply_right", 2: "k_s2_apply_left", 3: "util", 4: "stage1"}
+
+
+class hts_kernel_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
 class HTSError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -74,6 +83,12 @@ def load(path: str = LIB_PATH):
     lib.hts_sync_status.restype = _I
     lib.hts_status_string.argtypes = [_I]
     lib.hts_status_string.restype = ctypes.c_char_p
+    lib.hts_profile_begin.argtypes = [_VP, _I]
+    lib.hts_profile_begin.restype = _I
+    lib.hts_profile_end.argtypes = [_VP, ctypes.POINTER(hts_kernel_profile), ctypes.POINTER(ctypes.c_int)]
+    lib.hts_profile_end.restype = _I
+    lib.hts_probe_fp64_peak.argtypes = [_VP, ctypes.POINTER(ctypes.c_double)]
+    lib.hts_probe_fp64_peak.restype = _I
     _lib = lib
     return lib
 
@@ -166,3 +181,32 @@ def hts_sync_status(ctx, stream=None):
     info = (ctypes.c_int * 4)()
     st = load().hts_sync_status(ctx, _stream(stream), info)
     return st, list(info)
+
+
+def hts_profile_begin(ctx, max_launches: int):
+    st = load().hts_profile_begin(ctx, int(max_launches))
+    if st != HTS_OK:
+        raise HTSError(st, "hts_profile_begin")
+
+
+def hts_profile_end(ctx):
+    """Returns ({kind name: {launches, ms, flops, bytes}}, dropped)."""
+    out = (hts_kernel_profile * HTS_K_NKINDS)()
+    dropped = ctypes.c_int(0)
+    st = load().hts_profile_end(ctx, out, ctypes.byref(dropped))
+    if st != HTS_OK:
+        raise HTSError(st, "hts_profile_end")
+    res = {}
+    for k in range(HTS_K_NKINDS):
+        if out[k].launches:
+            res[KERNEL_KINDS.get(k, "kind%d" % k)] = dict(launches=out[k].launches, ms=out[k].ms,
+                                                         flops=out[k].flops, bytes=out[k].bytes)
+    return res, dropped.value
+
+
+def hts_probe_fp64_peak(stream=None) -> float:
+    v = ctypes.c_double(0.0)
+    st = load().hts_probe_fp64_peak(_stream(stream), ctypes.byref(v))
+    if st != HTS_OK:
+        raise HTSError(st, "hts_probe_fp64_peak")
+    return v.value

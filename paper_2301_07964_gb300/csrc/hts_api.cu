@@ -66,6 +66,57 @@ hts_status check_common(hts_ctx *ctx, int n, int r, const double *A, int lda, co
 
 hts_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HTS_OK : HTS_ERR_CUDA; }
 
+// Algorithmic cost of one group's three launches, for the profiler.  Flops: 4 per element
+// and reflector (dot product + update).  Bytes: every element a launch must change is read
+// and written once (16 bytes).
+struct GroupCost {
+    double f_gen, b_gen, f_right, b_right, f_left, b_left;
+};
+
+GroupCost s2_group_cost(int n, int r, int j1, int qg, bool hasQ, bool hasZ)
+{
+    GroupCost c{};
+    const int jl = j1 + qg - 1;
+    const int kmax = nblocks_gen(n, r, j1) - 1;
+    for (int j = j1; j <= jl; ++j) {
+        const int kg = nblocks_gen(n, r, j);
+        for (int k = 0; k < kg; ++k) {
+            const StepGeom g = step_geom(n, r, j1, qg, k, j);
+            const double m = g.i2 - g.i1 + 1;
+            const double rowsA = imax(0, g.i3 - g.i4 + 1), rowsB = imax(0, g.i2 - g.i4 + 1);
+            double rq = 0.0;
+            for (int sr = 2; sr <= (int)m; ++sr) rq += 4.0 * sr * (sr - 1 + m);
+            c.f_gen += 8.0 * m * (j - j1) + 4.0 * m * m + rq + 4.0 * m * (rowsA + rowsB);
+            c.b_gen += 16.0 * (m * (rowsA + rowsB) + m * m + 2.0 * (m + j - j1));
+            const double above = g.i4 - 1;   // rows of A and B the apply phase updates
+            c.f_right += 4.0 * m * (2.0 * above + (hasZ ? n : 0) + (hasQ ? n : 0));
+            const int cutA = jl + imax(0, (k - 1) * r + 1);
+            const int cutB = imin(jl + (k + 1) * r, n);
+            c.f_left += 4.0 * m * ((double)imax(0, n - cutA) + imax(0, n - cutB));
+        }
+    }
+    // right: rows x of A and B from the first block they need to column n; Z, Q all of it
+    double elems = 0.0;
+    for (int x = 1; x <= n; ++x) {
+        const int kf = (x <= j1) ? 0 : (x - j1 - 1) / r + 2;
+        if (kf <= kmax) elems += n - (j1 + kf * r);
+    }
+    c.b_right = 16.0 * (2.0 * elems + ((hasZ ? 1 : 0) + (hasQ ? 1 : 0)) * (double)n * (n - j1));
+    // left: column c of A / B from row j1+1 down to the bottom of the lowest block it needs
+    double le = 0.0;
+    for (int isB = 0; isB < 2; ++isB)
+        for (int k = kmax; k >= 0; --k) {
+            const int cut = isB ? imin(jl + (k + 1) * r, n) : jl + imax(0, (k - 1) * r + 1);
+            const int cutn = (k < kmax) ? (isB ? imin(jl + (k + 2) * r, n) : jl + imax(0, k * r + 1)) : n;
+            // columns in (cut, cutn] have block k as their lowest block
+            const int ncol = imax(0, imin(cutn, n) - cut);
+            const int rows = imin(n, j1 + qg - 1 + (k + 1) * r) - j1;
+            le += (double)ncol * rows;
+        }
+    c.b_left = 16.0 * le;
+    return c;
+}
+
 }  // namespace
 
 // Stage 2 driver: the group loop of generate / apply launches.
@@ -96,7 +147,13 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         ga.epoch = (unsigned long long)(group + 1) << 32;
         ga.status = ctx->d_status;
         ga.stall = (flags & HTS_FLAG_TEST_STALL) ? 1 : 0;
-        if ((e = launch_s2_generate(ga, st)) != cudaSuccess) return HTS_ERR_CUDA;
+        const GroupCost gc = ctx->prof.enabled ? s2_group_cost(n, r, j1, qg, Q != nullptr, Z != nullptr)
+                                               : GroupCost{};
+        {
+            ProfScope ps(ctx, st);
+            if ((e = launch_s2_generate(ga, st)) != cudaSuccess) return HTS_ERR_CUDA;
+            ps.done(HTS_K_GENERATE, gc.f_gen, gc.b_gen);
+        }
 
         ApplyArgs aa;
         int nm = 0;
@@ -106,16 +163,26 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         if (Q) { aa.M[nm] = Q; aa.ld[nm] = ldq; aa.kind[nm] = 3; ++nm; }
         for (int i = nm; i < 4; ++i) { aa.M[i] = nullptr; aa.ld[i] = 1; aa.kind[i] = 0; }
         aa.n = n; aa.r = r; aa.j1 = j1; aa.qg = qg; aa.R = R; aa.status = ctx->d_status;
-        if ((e = launch_s2_apply_right(aa, nm, st)) != cudaSuccess) return HTS_ERR_CUDA;
+        {
+            ProfScope ps(ctx, st);
+            if ((e = launch_s2_apply_right(aa, nm, st)) != cudaSuccess) return HTS_ERR_CUDA;
+            ps.done(HTS_K_APPLY_RIGHT, gc.f_right, gc.b_right);
+        }
 
         LeftArgs la;
         la.A = A; la.B = B; la.lda = lda; la.ldb = ldb;
         la.n = n; la.r = r; la.j1 = j1; la.qg = qg; la.R = R; la.status = ctx->d_status;
-        if ((e = launch_s2_apply_left(la, st)) != cudaSuccess) return HTS_ERR_CUDA;
+        {
+            ProfScope ps(ctx, st);
+            if ((e = launch_s2_apply_left(la, st)) != cudaSuccess) return HTS_ERR_CUDA;
+            ps.done(HTS_K_APPLY_LEFT, gc.f_left, gc.b_left);
+        }
     }
     if (!(flags & HTS_FLAG_NO_CLEAN)) {
+        ProfScope ps(ctx, st);
         if ((e = launch_zero_below(A, lda, n, 1, st)) != cudaSuccess) return HTS_ERR_CUDA;
         if ((e = launch_zero_below(B, ldb, n, 0, st)) != cudaSuccess) return HTS_ERR_CUDA;
+        ps.done(HTS_K_UTIL, 0.0, 0.0);
     }
     return HTS_OK;
 }
@@ -166,6 +233,10 @@ void hts_destroy(hts_ctx *ctx)
 {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
+    if (ctx->prof.cap > 0) {
+        hts_kernel_profile tmp[HTS_K_NKINDS];
+        hts_profile_end(ctx, tmp, nullptr);
+    }
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     std::free(ctx);
@@ -201,8 +272,12 @@ hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, dou
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     double *Qp = compq == HTS_COMP_NONE ? nullptr : Q;
     double *Zp = compz == HTS_COMP_NONE ? nullptr : Z;
-    if (compq == HTS_COMP_INIT && (s = cuda_status(launch_set_identity(Q, ldq, n, st))) != HTS_OK) return s;
-    if (compz == HTS_COMP_INIT && (s = cuda_status(launch_set_identity(Z, ldz, n, st))) != HTS_OK) return s;
+    if (compq == HTS_COMP_INIT || compz == HTS_COMP_INIT) {
+        ProfScope ps(ctx, st);
+        if (compq == HTS_COMP_INIT && (s = cuda_status(launch_set_identity(Q, ldq, n, st))) != HTS_OK) return s;
+        if (compz == HTS_COMP_INIT && (s = cuda_status(launch_set_identity(Z, ldz, n, st))) != HTS_OK) return s;
+        ps.done(HTS_K_UTIL, 0.0, 0.0);
+    }
     return run_stage2(ctx, n, r, A, lda, B, ldb, Qp, ldq, Zp, ldz, q, flags, work, st);
 }
 

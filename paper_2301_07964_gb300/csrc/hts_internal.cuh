@@ -8,11 +8,22 @@
 #include <stdint.h>
 
 #include "../../include/hts.h"
+#include "../../include/hts_profile.h"
+
+// Per-launch CUDA-event records of the optional profiler (include/hts_profile.h).
+struct hts_prof_state {
+    int enabled;
+    int cap, used, dropped;
+    cudaEvent_t *ev;     // 2 * cap events: start, end of launch i
+    int *kind;
+    double *flops, *bytes;
+};
 
 struct hts_ctx {
     int device;
     int *d_status;   // device status word: [0] code, [1..4] {pencil, group, k, j}
     int *h_status;   // pinned host mirror used by hts_sync_status
+    hts_prof_state prof;
 };
 
 namespace hts {
@@ -150,6 +161,15 @@ __device__ __forceinline__ double warp_larfg(double xi, int m, int lane, double 
     *vi = (lane == 0) ? 1.0 : ((lane < m) ? xi * sc : 0.0);
     return tau;
 }
+
+// Brackets one kernel launch with profiler events when profiling is on (profile.cu).
+struct ProfScope {
+    hts_ctx *ctx;
+    cudaStream_t st;
+    int idx;
+    ProfScope(hts_ctx *c, cudaStream_t s);
+    void done(int kind, double flops, double bytes);
+};
 
 // Arguments of the stage-2 launches (kernels in stage2.cu).
 struct GenArgs {
