@@ -120,6 +120,29 @@ hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r,
                              void *work, size_t work_bytes, void *stream);
 
 /*
+ * Stage 2 without a caller-provided workspace, for callers that cannot allocate device
+ * memory when they need the reduction (services that must not allocate once running, code
+ * inside a host framework that owns all device memory and lends out only the matrices).
+ * The paper has no counterpart: this is a deployment variant of hts_reduce_stage2 with the
+ * same arguments minus work / work_bytes and the same results.
+ *  - Scratch lives in one fixed 8 MiB array compiled into the library; every GPU that loads
+ *    the library holds it until the process exits.  Sizes whose workspace
+ *    (hts_workspace_size) exceeds 8 MiB are rejected with HTS_ERR_WORKSPACE before anything
+ *    runs (r = 16 allows n up to about 30000, r = 32 up to about 15000).
+ *  - The call allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *    with that device current); make that first call before any stream capture.
+ *  - All calls on a device share the array and it keeps the last call's contents (each call
+ *    clears what must start at zero).  Calls that overlap on the GPU (other streams, other
+ *    threads) race on it: serialise them.
+ */
+hts_status hts_reduce_stage2_noalloc(hts_ctx *ctx, int n, int r,
+                                     double *A, int lda, double *B, int ldb,
+                                     hts_comp compq, double *Q, int ldq,
+                                     hts_comp compz, double *Z, int ldz,
+                                     hts_gemm_mode mode, const hts_params *p, void *stream);
+
+/*
  * Full reduction of a dense pencil: QR of B (stage 0; the paper QR-factorises B first,
  * Section "Experiments"), then stage 1 with n_b = r, then stage 2.  Requires 1 <= r < n.
  */

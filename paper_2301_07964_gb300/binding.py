@@ -79,6 +79,8 @@ def load(path: str = LIB_PATH):
         f = getattr(lib, name)
         f.argtypes = _RED_ARGS
         f.restype = _I
+    lib.hts_reduce_stage2_noalloc.argtypes = _RED_ARGS[:15] + [_VP]
+    lib.hts_reduce_stage2_noalloc.restype = _I
     lib.hts_sync_status.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int)]
     lib.hts_sync_status.restype = _I
     lib.hts_status_string.argtypes = [_I]
@@ -168,6 +170,14 @@ def hts_reduce_stage2(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, m
                       work_bytes, stream=None) -> int:
     return _reduce("hts_reduce_stage2", ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode,
                    params, work, work_bytes, stream)
+
+
+def hts_reduce_stage2_noalloc(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode, params,
+                              stream=None) -> int:
+    """Stage 2 with the library's fixed scratch array instead of a caller workspace."""
+    return load().hts_reduce_stage2_noalloc(ctx, int(n), int(r), _ptr(A), int(lda), _ptr(B), int(ldb),
+                                            int(compq), _ptr(Q), int(ldq), int(compz), _ptr(Z), int(ldz),
+                                            int(mode), _params(params), _stream(stream))
 
 
 def hts_reduce(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode, params, work,
