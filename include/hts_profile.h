@@ -16,10 +16,11 @@ extern "C" {
 /* Kernel classes reported by the profiler. */
 enum {
     HTS_K_GENERATE = 0,     /* near-diagonal chase (stage 2 generate phase) */
-    HTS_K_APPLY_RIGHT = 1,  /* delayed right updates of A, B, Z and Q (stage 2) */
+    HTS_K_APPLY_RIGHT = 1,  /* delayed right updates of A and B (stage 2) */
     HTS_K_APPLY_LEFT = 2,   /* delayed left updates of A and B (stage 2) */
     HTS_K_UTIL = 3,         /* identity initialisation, final zeroing */
     HTS_K_STAGE1 = 4,       /* stage 0 / stage 1 kernels */
+    HTS_K_APPLY_QZ = 5,     /* delayed right updates of Q and Z (stage 2, side stream) */
     HTS_K_NKINDS = 8
 };
 

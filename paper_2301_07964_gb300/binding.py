@@ -39,7 +39,8 @@ class hts_params(ctypes.Structure):
 
 
 HTS_K_NKINDS = 8
-KERNEL_KINDS = {0: "k_s2_generate", 1: "k_s2_apply_right", 2: "k_s2_apply_left", 3: "util", 4: "stage1"}
+KERNEL_KINDS = {0: "k_s2_generate", 1: "k_s2_apply_right", 2: "k_s2_apply_left", 3: "util", 4: "stage1",
+                5: "k_s2_apply_right_qz"}
 
 
 class hts_kernel_profile(ctypes.Structure):

@@ -24,10 +24,12 @@ struct DeviceGuard {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Workspace layout of stage 2 (reflectors of one group, progress words).
+// Workspace layout of stage 2: two reflector sets (group g uses set g mod 2, so the Q / Z
+// update of group g can still read its set while group g+1 generates into the other one) and
+// one progress word per sweep slot.
 struct S2Layout {
     int kdim, qmax;
-    size_t off_vq, off_tq, off_vz, off_tz, off_flags, total;
+    size_t off_vq[2], off_tq[2], off_vz[2], off_tz[2], off_flags, total;
 };
 
 S2Layout s2_layout(int n, int r)
@@ -38,10 +40,12 @@ S2Layout s2_layout(int n, int r)
     const size_t nv = (size_t)L.qmax * L.kdim * r * sizeof(double);
     const size_t nt = (size_t)L.qmax * L.kdim * sizeof(double);
     size_t o = 0;
-    L.off_vq = o; o = align_up(o + nv, 256);
-    L.off_tq = o; o = align_up(o + nt, 256);
-    L.off_vz = o; o = align_up(o + nv, 256);
-    L.off_tz = o; o = align_up(o + nt, 256);
+    for (int b = 0; b < 2; ++b) {
+        L.off_vq[b] = o; o = align_up(o + nv, 256);
+        L.off_tq[b] = o; o = align_up(o + nt, 256);
+        L.off_vz[b] = o; o = align_up(o + nv, 256);
+        L.off_tz[b] = o; o = align_up(o + nt, 256);
+    }
     L.off_flags = o; o = align_up(o + (size_t)L.qmax * sizeof(unsigned long long), 256);
     L.total = o;
     return L;
@@ -70,7 +74,7 @@ hts_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HTS_OK : HTS_E
 // and reflector (dot product + update).  Bytes: every element a launch must change is read
 // and written once (16 bytes).
 struct GroupCost {
-    double f_gen, b_gen, f_right, b_right, f_left, b_left;
+    double f_gen, b_gen, f_right, b_right, f_qz, b_qz, f_left, b_left;
 };
 
 GroupCost s2_group_cost(int n, int r, int j1, int qg, bool hasQ, bool hasZ)
@@ -89,7 +93,8 @@ GroupCost s2_group_cost(int n, int r, int j1, int qg, bool hasQ, bool hasZ)
             c.f_gen += 8.0 * m * (j - j1) + 4.0 * m * m + rq + 4.0 * m * (rowsA + rowsB);
             c.b_gen += 16.0 * (m * (rowsA + rowsB) + m * m + 2.0 * (m + j - j1));
             const double above = g.i4 - 1;   // rows of A and B the apply phase updates
-            c.f_right += 4.0 * m * (2.0 * above + (hasZ ? n : 0) + (hasQ ? n : 0));
+            c.f_right += 4.0 * m * 2.0 * above;
+            c.f_qz += 4.0 * m * ((hasZ ? n : 0) + (hasQ ? n : 0));
             const int cutA = jl + imax(0, (k - 1) * r + 1);
             const int cutB = imin(jl + (k + 1) * r, n);
             c.f_left += 4.0 * m * ((double)imax(0, n - cutA) + imax(0, n - cutB));
@@ -101,7 +106,8 @@ GroupCost s2_group_cost(int n, int r, int j1, int qg, bool hasQ, bool hasZ)
         const int kf = (x <= j1) ? 0 : (x - j1 - 1) / r + 2;
         if (kf <= kmax) elems += n - (j1 + kf * r);
     }
-    c.b_right = 16.0 * (2.0 * elems + ((hasZ ? 1 : 0) + (hasQ ? 1 : 0)) * (double)n * (n - j1));
+    c.b_right = 16.0 * 2.0 * elems;
+    c.b_qz = 16.0 * ((hasZ ? 1 : 0) + (hasQ ? 1 : 0)) * (double)n * (n - j1);
     // left: column c of A / B from row j1+1 down to the bottom of the lowest block it needs
     double le = 0.0;
     for (int isB = 0; isB < 2; ++isB)
@@ -127,28 +133,36 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
     if (n <= 2 || r <= 1) return HTS_OK;
     const S2Layout L = s2_layout(n, r);
     char *w = static_cast<char *>(work);
-    ReflectorSet R;
-    R.VQ = reinterpret_cast<double *>(w + L.off_vq);
-    R.TQ = reinterpret_cast<double *>(w + L.off_tq);
-    R.VZ = reinterpret_cast<double *>(w + L.off_vz);
-    R.TZ = reinterpret_cast<double *>(w + L.off_tz);
-    R.kdim = L.kdim;
+    ReflectorSet R[2];
+    for (int b = 0; b < 2; ++b) {
+        R[b].VQ = reinterpret_cast<double *>(w + L.off_vq[b]);
+        R[b].TQ = reinterpret_cast<double *>(w + L.off_tq[b]);
+        R[b].VZ = reinterpret_cast<double *>(w + L.off_vz[b]);
+        R[b].TZ = reinterpret_cast<double *>(w + L.off_tz[b]);
+        R[b].kdim = L.kdim;
+    }
     unsigned long long *fl = reinterpret_cast<unsigned long long *>(w + L.off_flags);
     cudaError_t e = cudaMemsetAsync(fl, 0, (size_t)L.qmax * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return HTS_ERR_CUDA;
+    const bool qz = (Q != nullptr) || (Z != nullptr);
+    cudaStream_t side = ctx->side;
 
     int group = 0;
     for (int j1 = 1; j1 <= n - 2; j1 += q, ++group) {
         const int qg = imin(q, n - 2 - j1 + 1);
+        const int set = group & 1;
+        const GroupCost gc = ctx->prof.enabled ? s2_group_cost(n, r, j1, qg, Q != nullptr, Z != nullptr)
+                                               : GroupCost{};
+        // the Q / Z update of group-2 must be done with this reflector set
+        if (qz && group >= 2 && cudaStreamWaitEvent(st, ctx->ev_qz[set], 0) != cudaSuccess) return HTS_ERR_CUDA;
+
         GenArgs ga;
         ga.A = A; ga.B = B; ga.lda = lda; ga.ldb = ldb;
         ga.n = n; ga.r = r; ga.j1 = j1; ga.qg = qg; ga.group = group;
-        ga.R = R; ga.flags = fl;
+        ga.R = R[set]; ga.flags = fl;
         ga.epoch = (unsigned long long)(group + 1) << 32;
         ga.status = ctx->d_status;
         ga.stall = (flags & HTS_FLAG_TEST_STALL) ? 1 : 0;
-        const GroupCost gc = ctx->prof.enabled ? s2_group_cost(n, r, j1, qg, Q != nullptr, Z != nullptr)
-                                               : GroupCost{};
         {
             ProfScope ps(ctx, st);
             if ((e = launch_s2_generate(ga, st)) != cudaSuccess) return HTS_ERR_CUDA;
@@ -156,28 +170,47 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         }
 
         ApplyArgs aa;
-        int nm = 0;
-        aa.M[nm] = A; aa.ld[nm] = lda; aa.kind[nm] = 0; ++nm;
-        aa.M[nm] = B; aa.ld[nm] = ldb; aa.kind[nm] = 1; ++nm;
-        if (Z) { aa.M[nm] = Z; aa.ld[nm] = ldz; aa.kind[nm] = 2; ++nm; }
-        if (Q) { aa.M[nm] = Q; aa.ld[nm] = ldq; aa.kind[nm] = 3; ++nm; }
-        for (int i = nm; i < 4; ++i) { aa.M[i] = nullptr; aa.ld[i] = 1; aa.kind[i] = 0; }
-        aa.n = n; aa.r = r; aa.j1 = j1; aa.qg = qg; aa.R = R; aa.status = ctx->d_status;
+        aa.M[0] = A; aa.ld[0] = lda; aa.kind[0] = 0;
+        aa.M[1] = B; aa.ld[1] = ldb; aa.kind[1] = 1;
+        for (int i = 2; i < 4; ++i) { aa.M[i] = nullptr; aa.ld[i] = 1; aa.kind[i] = 0; }
+        aa.n = n; aa.r = r; aa.j1 = j1; aa.qg = qg; aa.R = R[set]; aa.status = ctx->d_status;
         {
             ProfScope ps(ctx, st);
-            if ((e = launch_s2_apply_right(aa, nm, st)) != cudaSuccess) return HTS_ERR_CUDA;
+            if ((e = launch_s2_apply_right(aa, 2, st)) != cudaSuccess) return HTS_ERR_CUDA;
             ps.done(HTS_K_APPLY_RIGHT, gc.f_right, gc.b_right);
         }
 
         LeftArgs la;
         la.A = A; la.B = B; la.lda = lda; la.ldb = ldb;
-        la.n = n; la.r = r; la.j1 = j1; la.qg = qg; la.R = R; la.status = ctx->d_status;
+        la.n = n; la.r = r; la.j1 = j1; la.qg = qg; la.R = R[set]; la.status = ctx->d_status;
         {
             ProfScope ps(ctx, st);
             if ((e = launch_s2_apply_left(la, st)) != cudaSuccess) return HTS_ERR_CUDA;
             ps.done(HTS_K_APPLY_LEFT, gc.f_left, gc.b_left);
         }
+        // Q and Z: on the side stream after this group's A / B updates, so that they overlap
+        // the next group's chase (which occupies only qg SMs) and not the A / B updates
+        if (qz) {
+            if (cudaEventRecord(ctx->ev_gen[set], st) != cudaSuccess) return HTS_ERR_CUDA;
+            if (cudaStreamWaitEvent(side, ctx->ev_gen[set], 0) != cudaSuccess) return HTS_ERR_CUDA;
+            ApplyArgs aq;
+            int nq = 0;
+            if (Z) { aq.M[nq] = Z; aq.ld[nq] = ldz; aq.kind[nq] = 2; ++nq; }
+            if (Q) { aq.M[nq] = Q; aq.ld[nq] = ldq; aq.kind[nq] = 3; ++nq; }
+            for (int i = nq; i < 4; ++i) { aq.M[i] = nullptr; aq.ld[i] = 1; aq.kind[i] = 0; }
+            aq.n = n; aq.r = r; aq.j1 = j1; aq.qg = qg; aq.R = R[set]; aq.status = ctx->d_status;
+            {
+                ProfScope ps(ctx, side);
+                if ((e = launch_s2_apply_right(aq, nq, side)) != cudaSuccess) return HTS_ERR_CUDA;
+                ps.done(HTS_K_APPLY_QZ, gc.f_qz, gc.b_qz);
+            }
+            if (cudaEventRecord(ctx->ev_qz[set], side) != cudaSuccess) return HTS_ERR_CUDA;
+        }
+
     }
+    // the caller's stream resumes only after the last Q / Z update
+    if (qz && group >= 1 && cudaStreamWaitEvent(st, ctx->ev_qz[(group - 1) & 1], 0) != cudaSuccess)
+        return HTS_ERR_CUDA;
     if (!(flags & HTS_FLAG_NO_CLEAN)) {
         ProfScope ps(ctx, st);
         if ((e = launch_zero_below(A, lda, n, 1, st)) != cudaSuccess) return HTS_ERR_CUDA;
@@ -218,11 +251,17 @@ hts_status hts_create(hts_ctx **ctx, int device)
     hts_ctx *c = static_cast<hts_ctx *>(std::calloc(1, sizeof(hts_ctx)));
     if (!c) return HTS_ERR_CUDA;
     c->device = device;
-    if (cudaMalloc(&c->d_status, kStatusWords * sizeof(int)) != cudaSuccess ||
-        cudaMemset(c->d_status, 0, kStatusWords * sizeof(int)) != cudaSuccess ||
-        cudaMallocHost(&c->h_status, kStatusWords * sizeof(int)) != cudaSuccess) {
-        if (c->d_status) cudaFree(c->d_status);
-        std::free(c);
+    int lo_prio = 0, hi_prio = 0;
+    bool ok = cudaMalloc(&c->d_status, kStatusWords * sizeof(int)) == cudaSuccess &&
+              cudaMemset(c->d_status, 0, kStatusWords * sizeof(int)) == cudaSuccess &&
+              cudaMallocHost(&c->h_status, kStatusWords * sizeof(int)) == cudaSuccess &&
+              cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, lo_prio) == cudaSuccess;
+    for (int b = 0; ok && b < 2; ++b)
+        ok = cudaEventCreateWithFlags(&c->ev_gen[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_qz[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        hts_destroy(c);
         return HTS_ERR_CUDA;
     }
     *ctx = c;
@@ -237,6 +276,12 @@ void hts_destroy(hts_ctx *ctx)
         hts_kernel_profile tmp[HTS_K_NKINDS];
         hts_profile_end(ctx, tmp, nullptr);
     }
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
+    for (int b = 0; b < 2; ++b) {
+        if (ctx->ev_gen[b]) cudaEventDestroy(ctx->ev_gen[b]);
+        if (ctx->ev_qz[b]) cudaEventDestroy(ctx->ev_qz[b]);
+    }
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     std::free(ctx);

@@ -24,6 +24,11 @@ struct hts_ctx {
     int *d_status;   // device status word: [0] code, [1..4] {pencil, group, k, j}
     int *h_status;   // pinned host mirror used by hts_sync_status
     hts_prof_state prof;
+    // Second stream for the Q / Z updates, which overlap the next group's chase, and the
+    // events that order it against the caller's stream (created once by hts_create).
+    cudaStream_t side;
+    cudaEvent_t ev_gen[2];   // reflector set s written (generate done)
+    cudaEvent_t ev_qz[2];    // reflector set s no longer read (Q / Z update done)
 };
 
 namespace hts {
@@ -31,7 +36,7 @@ namespace hts {
 constexpr int kStatusWords = 8;
 constexpr int kMaxR = 32;            // reflector length limit of the warp-level chase
 constexpr int kGenThreads = 256;     // threads of one generate (chase) block
-constexpr int kApplyThreads = 128;   // threads (rows or columns) of one apply block
+constexpr int kApplyThreads = 64;    // threads (rows or columns) of one apply block
 constexpr long long kSpinLimit = 1LL << 24;   // bounded waits: polls before giving up
 constexpr unsigned long long kWaitLimitNs = 2000000000ULL;   // ... or 2 s of wall clock
 
@@ -209,5 +214,37 @@ cudaError_t launch_s2_apply_right(const ApplyArgs &a, int nmat, cudaStream_t st)
 cudaError_t launch_s2_apply_left(const LeftArgs &a, cudaStream_t st);
 cudaError_t launch_set_identity(double *M, int ld, int n, cudaStream_t st);
 cudaError_t launch_zero_below(double *M, int ld, int n, int band, cudaStream_t st);
+
+// Same reflector as warp_larfg with one reciprocal square root and one reciprocal on the
+// dependent path: with rs = 1/||x||, beta = -sign(alpha) ||x||, tau = 1 + |alpha| rs and
+// v_i = x_i sign(alpha) rs / tau.  Falls back to the scaled form when the sum of squares
+// leaves the safe range.
+__device__ __forceinline__ double warp_larfg_fast(double xi, int m, int lane, double *beta, double *vi)
+{
+    const double alpha = __shfl_sync(0xffffffffu, xi, 0);
+    const double t = (lane >= 1 && lane < m) ? xi : 0.0;
+    const double ssq = warp_sum(t * t);
+    if (ssq == 0.0) {
+        *beta = alpha;
+        *vi = (lane == 0) ? 1.0 : 0.0;
+        return 0.0;
+    }
+    if (!(ssq >= 1e-290 && ssq <= 1e290) || fabs(alpha) > 1e145) return warp_larfg(xi, m, lane, beta, vi);
+    const double nrm2 = fma(alpha, alpha, ssq);
+    const double rs = rsqrt(nrm2);
+    const double sa = alpha >= 0.0 ? 1.0 : -1.0;
+    const double tau = fma(fabs(alpha), rs, 1.0);
+    *beta = -sa * (nrm2 * rs);
+    const double sc = sa * rs * __drcp_rn(tau);
+    *vi = (lane == 0) ? 1.0 : ((lane < m) ? xi * sc : 0.0);
+    return tau;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 }  // namespace hts

@@ -96,7 +96,8 @@ hts_status hts_profile_end(hts_ctx *ctx, hts_kernel_profile out[HTS_K_NKINDS], i
     for (int k = 0; k < HTS_K_NKINDS; ++k) out[k] = hts_kernel_profile{};
     if (dropped) *dropped = p.dropped;
     hts_status st = HTS_OK;
-    if (p.used > 0 && cudaEventSynchronize(p.ev[2 * p.used - 1]) != cudaSuccess) st = HTS_ERR_CUDA;
+    for (int i = 0; st == HTS_OK && i < p.used; ++i)   // launches may sit on two streams
+        if (cudaEventSynchronize(p.ev[2 * i + 1]) != cudaSuccess) st = HTS_ERR_CUDA;
     for (int i = 0; st == HTS_OK && i < p.used; ++i) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]) != cudaSuccess) {
