@@ -59,7 +59,8 @@ typedef enum {
 /* Tuning parameters; 0 selects the library default.
  *  q          sweeps grouped per generate/apply iteration (Section "Blocked stage two");
  *             1 <= q <= r.  Default: r.
- *  p          stage-1 block height in units of r (Alg. 1); p >= 2.  Default: 8.
+ *  p          stage-1 block height in units of r (Alg. 1); p >= 2 and p*r <= 128 (one
+ *             block's RQ runs in shared memory).  Default: min(8, 128/r).
  *  emu_slices number of BF16 slices per FP64 operand in HTS_GEMM_EMU_BF16 mode.
  *  tile_m, tile_n  reserved.
  *  flags      bit 0 (HTS_FLAG_NO_CLEAN): skip the final exact zeroing below the band.
@@ -94,8 +95,11 @@ void hts_destroy(hts_ctx *ctx);
 hts_status hts_workspace_size(int n, int r, const hts_params *p, size_t *bytes);
 
 /*
- * Stage 1: Alg. 1 of the paper ("Blocked stage 1").  Requires B upper triangular (its
- * strictly lower part is ignored and zeroed) and 1 <= r < n.  On exit (A, B) is in r-HT form.
+ * Stage 1: Alg. 1 of the paper ("Blocked stage 1") with n_b = r.  Requires B upper
+ * triangular (its strictly lower part is ignored and zeroed) and 1 <= r < n, r <= 64.  On
+ * exit (A, B) is in r-HT form with exact zeros below the r-th subdiagonal of A and below the
+ * diagonal of B.  The block reflectors are applied in compact WY form (native FP64);
+ * HTS_GEMM_EMU_BF16 returns HTS_ERR_UNSUPPORTED.
  */
 hts_status hts_reduce_stage1(hts_ctx *ctx, int n, int r,
                              double *A, int lda, double *B, int ldb,
@@ -144,7 +148,8 @@ hts_status hts_reduce_stage2_noalloc(hts_ctx *ctx, int n, int r,
 
 /*
  * Full reduction of a dense pencil: QR of B (stage 0; the paper QR-factorises B first,
- * Section "Experiments"), then stage 1 with n_b = r, then stage 2.  Requires 1 <= r < n.
+ * Section "Experiments"), then stage 1 with n_b = r, then stage 2.  Requires 1 <= r < n and
+ * r <= 32.  With HTS_COMP_INIT, Q e_1 = +-B(:,1)/||B(:,1)|| and Z e_1 = e_1.
  */
 hts_status hts_reduce(hts_ctx *ctx, int n, int r,
                       double *A, int lda, double *B, int ldb,

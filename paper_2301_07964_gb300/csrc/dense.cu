@@ -1,0 +1,337 @@
+// Dense FP64 building blocks of stages 0 and 1 (QR of B, Alg. 1): a tiled GEMM, Householder
+// QR of a panel, the triangular factor of a block reflector (forward, columnwise), and the
+// RQ + LQ factorisation of one B block that yields the opposite reflectors of Alg. 1.
+//
+// Block reflectors are used in compact WY form: H_1 H_2 ... H_b = I - V T V^T with V unit
+// lower trapezoidal (explicit ones and zeros) and T upper triangular (both dense buffers).
+#include "hts_internal.cuh"
+
+namespace hts {
+
+// ---------------------------------------------------------------------------------------
+// C = alpha op(A) op(B) + beta C, column-major, op(A) M x K, op(B) K x N.  beta = 0 does not
+// read C.  64 x 64 tiles, 256 threads, 4 x 4 outputs per thread, FP64 FMA.
+// ---------------------------------------------------------------------------------------
+constexpr int kGM = 64, kGN = 64, kGK = 16;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha, const double *A, int lda,
+                                               const double *B, int ldb, double beta, double *C, int ldc)
+{
+    __shared__ double As[kGK][kGM + 1];
+    __shared__ double Bs[kGK][kGN + 1];
+    const int tid = threadIdx.x;
+    const int m0 = blockIdx.x * kGM, n0 = blockIdx.y * kGN;
+    const int tm = (tid % 16) * 4, tn = (tid / 16) * 4;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += kGK) {
+        for (int e = tid; e < kGM * kGK; e += 256) {
+            int mm, kk;
+            if (!TA) { mm = e % kGM; kk = e / kGM; }
+            else { kk = e % kGK; mm = e / kGK; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            double v = 0.0;
+            if (gm < M && gk < K) v = TA ? A[(size_t)gk + (size_t)gm * lda] : A[(size_t)gm + (size_t)gk * lda];
+            As[kk][mm] = v;
+        }
+        for (int e = tid; e < kGN * kGK; e += 256) {
+            int nn, kk;
+            if (!TB) { kk = e % kGK; nn = e / kGK; }
+            else { nn = e % kGN; kk = e / kGN; }
+            const int gn = n0 + nn, gk = k0 + kk;
+            double v = 0.0;
+            if (gn < N && gk < K) v = TB ? B[(size_t)gn + (size_t)gk * ldb] : B[(size_t)gk + (size_t)gn * ldb];
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kGK; ++kk) {
+            double a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][tm + i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) bb[i] = Bs[kk][tn + i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(a[i], bb[jj], acc[i][jj]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int gm = m0 + tm + i, gn = n0 + tn + jj;
+            if (gm < M && gn < N) {
+                double *c = C + (size_t)gm + (size_t)gn * ldc;
+                *c = (beta == 0.0) ? alpha * acc[i][jj] : alpha * acc[i][jj] + beta * (*c);
+            }
+        }
+}
+
+cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda,
+                  const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t st)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    dim3 grid((M + kGM - 1) / kGM, (N + kGN - 1) / kGN);
+    if (!ta && !tb) k_dgemm<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    else if (ta && !tb) k_dgemm<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    else if (!ta && tb) k_dgemm<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    else k_dgemm<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Householder QR of the m x b panel P (column-major, ld) in one thread block (dlarfg
+// convention).  On exit the upper triangle of P holds R; V (m x b, ldv) receives the unit
+// lower trapezoidal reflector vectors and tau[0..b) the factors; the entries of P below the
+// diagonal are set to zero.
+// ---------------------------------------------------------------------------------------
+constexpr int kPanelThreads = 256;
+
+__device__ double block_sum(double v, double *red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
+__global__ void __launch_bounds__(kPanelThreads) k_panel_qr(int m, int b, double *P, int ld, double *V, int ldv,
+                                                             double *tau)
+{
+    __shared__ double red[32];
+    __shared__ double s_beta, s_tau, s_scale;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = kPanelThreads / 32;
+    for (int c = 0; c < b && c < m; ++c) {
+        // reflector from P(c:m, c)
+        double part = 0.0;
+        for (int i = c + 1 + tid; i < m; i += kPanelThreads) {
+            const double x = P[(size_t)i + (size_t)c * ld];
+            part += x * x;
+        }
+        const double ssq = block_sum(part, red);
+        if (tid == 0) {
+            const double alpha = P[(size_t)c + (size_t)c * ld];
+            if (ssq == 0.0) {
+                s_tau = 0.0;
+                s_beta = alpha;
+                s_scale = 0.0;
+            } else {
+                const double nrm = sqrt(alpha * alpha + ssq);
+                const double beta = (alpha >= 0.0) ? -nrm : nrm;
+                s_tau = (beta - alpha) / beta;
+                s_scale = 1.0 / (alpha - beta);
+                s_beta = beta;
+            }
+            tau[c] = s_tau;
+        }
+        __syncthreads();
+        const double tc = s_tau, sc = s_scale;
+        for (int i = tid; i < m; i += kPanelThreads) {
+            double vi;
+            if (i < c) vi = 0.0;
+            else if (i == c) vi = 1.0;
+            else vi = P[(size_t)i + (size_t)c * ld] * sc;
+            if (tc == 0.0 && i > c) vi = 0.0;
+            V[(size_t)i + (size_t)c * ldv] = vi;
+        }
+        __syncthreads();
+        if (tid == 0) P[(size_t)c + (size_t)c * ld] = s_beta;
+        for (int i = c + 1 + tid; i < m; i += kPanelThreads) P[(size_t)i + (size_t)c * ld] = 0.0;
+        // apply to the remaining panel columns (one warp per column)
+        if (tc != 0.0) {
+            for (int cc = c + 1 + warp; cc < b; cc += nw) {
+                double d = 0.0;
+                for (int i = c + lane; i < m; i += 32) d += V[(size_t)i + (size_t)c * ldv] * P[(size_t)i + (size_t)cc * ld];
+                d = warp_sum(d) * tc;
+                for (int i = c + lane; i < m; i += 32) P[(size_t)i + (size_t)cc * ld] -= d * V[(size_t)i + (size_t)c * ldv];
+            }
+        }
+        __syncthreads();
+    }
+    for (int c = m; c < b; ++c) {   // more columns than rows: nothing left to reduce
+        if (tid == 0) tau[c] = 0.0;
+        for (int i = tid; i < m; i += kPanelThreads) V[(size_t)i + (size_t)c * ldv] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// T (b x b, ldt) of H_1 ... H_b = I - V T V^T from S = V^T V (b x b) and tau: forward,
+// columnwise: T(i, i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) S(0:i, i).  One thread block.
+// ---------------------------------------------------------------------------------------
+__global__ void k_larft(int b, const double *S, int lds, const double *tau, double *T, int ldt)
+{
+    __shared__ double tmp[256];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < b * b; e += blockDim.x) T[(e % b) + (size_t)(e / b) * ldt] = 0.0;
+    __syncthreads();
+    for (int i = 0; i < b; ++i) {
+        const double ti = tau[i];
+        // w = S(0:i, i) -> tmp; T(0:i, i) = -ti T(0:i, 0:i) w
+        for (int e = tid; e < i; e += blockDim.x) tmp[e] = S[e + (size_t)i * lds];
+        __syncthreads();
+        for (int row = tid; row < i; row += blockDim.x) {
+            double acc = 0.0;
+            for (int l = row; l < i; ++l) acc += T[row + (size_t)l * ldt] * tmp[l];
+            T[row + (size_t)i * ldt] = -ti * acc;
+        }
+        if (tid == 0) T[i + (size_t)i * ldt] = ti;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Opposite reflectors of one filled B block (Alg. 1, right-hand part): RQ of the m x m block
+// W = R~ Q~ (Householder, last row first, reflectors kept in the zeroed part of W), then the
+// LQ factorisation of the first l rows of Q~; the LQ reflectors (unit upper... stored as
+// columns of V, m x l, unit lower trapezoidal in the block's column index) and tau_lq are
+// returned.  Applying H_1 ... H_l from the right reduces the first l columns of the block.
+// One thread block; W and the l x m matrix M = Q~(0:l, :) live in shared memory.
+// ---------------------------------------------------------------------------------------
+constexpr int kRQThreads = 512;
+
+__global__ void __launch_bounds__(kRQThreads) k_block_rq_lq(int m, int l, const double *Bblk, int ldb,
+                                                             double *V, int ldv, double *tau_lq)
+{
+    extern __shared__ double sh[];
+    const int ldw = m + 1;
+    double *W = sh;                          // m x m, row-major: W[i * ldw + c]
+    double *Ms = W + (size_t)m * ldw;        // l x m, row-major
+    double *rqt = Ms + (size_t)l * ldw;      // m taus of the RQ reflectors
+    double *vec = rqt + m;                   // m
+    __shared__ double red[32];
+    __shared__ double s_tau, s_beta, s_scale;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = kRQThreads / 32;
+
+    for (int e = tid; e < m * m; e += kRQThreads) {
+        const int i = e % m, c = e / m;
+        W[i * ldw + c] = Bblk[(size_t)i + (size_t)c * ldb];
+    }
+    __syncthreads();
+    // RQ: for s = m-1 .. 1 (0-based pivot row s, pivot column s)
+    for (int s = m - 1; s >= 1; --s) {
+        double part = 0.0;
+        for (int c = tid; c < s; c += kRQThreads) part += W[s * ldw + c] * W[s * ldw + c];
+        const double ssq = block_sum(part, red);
+        if (tid == 0) {
+            const double alpha = W[s * ldw + s];
+            if (ssq == 0.0) {
+                s_tau = 0.0; s_beta = alpha; s_scale = 0.0;
+            } else {
+                const double nrm = sqrt(alpha * alpha + ssq);
+                const double beta = (alpha >= 0.0) ? -nrm : nrm;
+                s_tau = (beta - alpha) / beta;
+                s_scale = 1.0 / (alpha - beta);
+                s_beta = beta;
+            }
+            rqt[s] = s_tau;
+        }
+        __syncthreads();
+        const double ts = s_tau;
+        // reflector vector (v_s = 1, v_c = W(s, c) * scale for c < s) kept in row s
+        for (int c = tid; c < s; c += kRQThreads) W[s * ldw + c] *= s_scale;
+        __syncthreads();
+        if (ts != 0.0) {
+            for (int row = warp; row < s; row += nw) {
+                double d = 0.0;
+                for (int c = lane; c <= s; c += 32) d += W[row * ldw + c] * (c == s ? 1.0 : W[s * ldw + c]);
+                d = warp_sum(d) * ts;
+                for (int c = lane; c <= s; c += 32) W[row * ldw + c] -= d * (c == s ? 1.0 : W[s * ldw + c]);
+            }
+        }
+        if (tid == 0) W[s * ldw + s] = s_beta;
+        __syncthreads();
+    }
+    // M = E_l^T H_1' H_2' ... with the RQ reflectors in the order that forms Q~ = G^T:
+    // Q~ = H_(1) H_(2) ... H_(m-1) where H_(s) acts on columns 0..s; row block 0..l-1 of it
+    for (int e = tid; e < l * m; e += kRQThreads) {
+        const int t = e / m, c = e % m;
+        Ms[t * ldw + c] = (t == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int s = 1; s <= m - 1; ++s) {
+        const double ts = rqt[s];
+        if (ts != 0.0) {
+            for (int t = warp; t < l; t += nw) {
+                double d = 0.0;
+                for (int c = lane; c <= s; c += 32) d += Ms[t * ldw + c] * (c == s ? 1.0 : W[s * ldw + c]);
+                d = warp_sum(d) * ts;
+                for (int c = lane; c <= s; c += 32) Ms[t * ldw + c] -= d * (c == s ? 1.0 : W[s * ldw + c]);
+            }
+        }
+        __syncthreads();
+    }
+    // LQ of M (l x m): reflector t reduces M(t, t:m) to beta e_1, applied to rows t+1..l-1
+    for (int t = 0; t < l; ++t) {
+        double part = 0.0;
+        for (int c = t + 1 + tid; c < m; c += kRQThreads) part += Ms[t * ldw + c] * Ms[t * ldw + c];
+        const double ssq = block_sum(part, red);
+        if (tid == 0) {
+            const double alpha = Ms[t * ldw + t];
+            if (ssq == 0.0) {
+                s_tau = 0.0; s_beta = alpha; s_scale = 0.0;
+            } else {
+                const double nrm = sqrt(alpha * alpha + ssq);
+                const double beta = (alpha >= 0.0) ? -nrm : nrm;
+                s_tau = (beta - alpha) / beta;
+                s_scale = 1.0 / (alpha - beta);
+                s_beta = beta;
+            }
+            tau_lq[t] = s_tau;
+        }
+        __syncthreads();
+        const double tt = s_tau, sc = s_scale;
+        for (int c = tid; c < m; c += kRQThreads) {
+            double vc;
+            if (c < t) vc = 0.0;
+            else if (c == t) vc = 1.0;
+            else vc = (tt == 0.0) ? 0.0 : Ms[t * ldw + c] * sc;
+            vec[c] = vc;
+            V[(size_t)c + (size_t)t * ldv] = vc;
+        }
+        __syncthreads();
+        if (tt != 0.0) {
+            for (int row = t + 1 + warp; row < l; row += nw) {
+                double d = 0.0;
+                for (int c = t + lane; c < m; c += 32) d += Ms[row * ldw + c] * vec[c];
+                d = warp_sum(d) * tt;
+                for (int c = t + lane; c < m; c += 32) Ms[row * ldw + c] -= d * vec[c];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+size_t block_rq_lq_smem(int m, int l) { return sizeof(double) * ((size_t)(m + l) * (m + 1) + 2 * (size_t)m); }
+
+cudaError_t launch_panel_qr(int m, int b, double *P, int ld, double *V, int ldv, double *tau, cudaStream_t st)
+{
+    k_panel_qr<<<1, kPanelThreads, 0, st>>>(m, b, P, ld, V, ldv, tau);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_larft(int b, const double *S, int lds, const double *tau, double *T, int ldt, cudaStream_t st)
+{
+    k_larft<<<1, 256, 0, st>>>(b, S, lds, tau, T, ldt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_rq_lq(int m, int l, const double *Bblk, int ldb, double *V, int ldv, double *tau_lq,
+                               cudaStream_t st)
+{
+    const size_t sm = block_rq_lq_smem(m, l);
+    cudaError_t e = cudaFuncSetAttribute(k_block_rq_lq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_block_rq_lq<<<1, kRQThreads, sm, st>>>(m, l, Bblk, ldb, V, ldv, tau_lq);
+    return cudaGetLastError();
+}
+
+}  // namespace hts

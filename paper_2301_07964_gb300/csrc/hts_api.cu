@@ -70,6 +70,15 @@ hts_status check_common(hts_ctx *ctx, int n, int r, const double *A, int lda, co
 
 hts_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HTS_OK : HTS_ERR_CUDA; }
 
+// Block height (in units of r) of stage 1: the paper's p = 8 by default, limited so that one
+// p*r x p*r B block fits in shared memory for its RQ (p*r <= 128).
+int stage1_p(const hts_params *prm, int r)
+{
+    const int cap = imax(2, 128 / imax(r, 1));
+    if (prm && prm->p > 0) return prm->p;
+    return imin(8, cap);
+}
+
 // Algorithmic cost of one group's three launches, for the profiler.  Flops: 4 per element
 // and reflector (dot product + update).  Bytes: every element a launch must change is read
 // and written once (16 bytes).
@@ -124,6 +133,9 @@ GroupCost s2_group_cost(int n, int r, int j1, int qg, bool hasQ, bool hasZ)
 }
 
 }  // namespace
+
+// Bytes of caller scratch stage 2 alone needs (two reflector sets and the progress words).
+size_t stage2_workspace_bytes(int n, int r) { return s2_layout(n, r).total; }
 
 // Stage 2 driver: the group loop of generate / apply launches.
 hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B, int ldb,
@@ -289,9 +301,10 @@ void hts_destroy(hts_ctx *ctx)
 
 hts_status hts_workspace_size(int n, int r, const hts_params *p, size_t *bytes)
 {
-    (void)p;
     if (!bytes || n < 0 || r < 1) return HTS_ERR_ARG;
-    *bytes = s2_layout(n, r).total;
+    const size_t s2 = s2_layout(n, r).total;
+    const size_t s01 = stage01_workspace_bytes(n, r, stage1_p(p, r));
+    *bytes = s2 > s01 ? s2 : s01;
     return HTS_OK;
 }
 
@@ -326,25 +339,85 @@ hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, dou
     return run_stage2(ctx, n, r, A, lda, B, ldb, Qp, ldq, Zp, ldz, q, flags, work, st);
 }
 
+static hts_status check_stage1_args(hts_ctx *ctx, int n, int r, const hts_params *p, void *work, size_t work_bytes)
+{
+    if (r >= n) return HTS_ERR_ARG;
+    if (r > 64) return HTS_ERR_UNSUPPORTED;
+    const int pp = stage1_p(p, r);
+    if (pp < 2) return HTS_ERR_ARG;
+    if (pp * r > 128) return HTS_ERR_UNSUPPORTED;
+    size_t need = 0;
+    hts_workspace_size(n, r, p, &need);
+    if (!work || (reinterpret_cast<uintptr_t>(work) & 255u) || work_bytes < need) return HTS_ERR_WORKSPACE;
+    (void)ctx;
+    return HTS_OK;
+}
+
 hts_status hts_reduce_stage1(hts_ctx *ctx, int n, int r, double *A, int lda, double *B, int ldb,
                              hts_comp compq, double *Q, int ldq, hts_comp compz, double *Z, int ldz,
                              hts_gemm_mode mode, const hts_params *p, void *work, size_t work_bytes,
                              void *stream)
 {
-    (void)p; (void)work; (void)work_bytes; (void)stream;
     hts_status s = check_common(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode);
     if (s != HTS_OK || n == 0) return s;
-    return HTS_ERR_UNSUPPORTED;
+    if (mode != HTS_GEMM_FP64) return HTS_ERR_UNSUPPORTED;
+    if ((s = check_stage1_args(ctx, n, r, p, work, work_bytes)) != HTS_OK) return s;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return HTS_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double *Qp = compq == HTS_COMP_NONE ? nullptr : Q;
+    double *Zp = compz == HTS_COMP_NONE ? nullptr : Z;
+    ProfScope ps(ctx, st);
+    if (compq == HTS_COMP_INIT && launch_set_identity(Q, ldq, n, st) != cudaSuccess) return HTS_ERR_CUDA;
+    if (compz == HTS_COMP_INIT && launch_set_identity(Z, ldz, n, st) != cudaSuccess) return HTS_ERR_CUDA;
+    if (launch_zero_below(B, ldb, n, 0, st) != cudaSuccess) return HTS_ERR_CUDA;
+    if (run_stage1(n, r, stage1_p(p, r), A, lda, B, ldb, Qp, ldq, Zp, ldz, work, st) != cudaSuccess)
+        return HTS_ERR_CUDA;
+    ps.done(HTS_K_STAGE1, 0.0, 0.0);
+    return HTS_OK;
 }
 
 hts_status hts_reduce(hts_ctx *ctx, int n, int r, double *A, int lda, double *B, int ldb,
                       hts_comp compq, double *Q, int ldq, hts_comp compz, double *Z, int ldz,
                       hts_gemm_mode mode, const hts_params *p, void *work, size_t work_bytes, void *stream)
 {
-    (void)p; (void)work; (void)work_bytes; (void)stream;
     hts_status s = check_common(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode);
     if (s != HTS_OK || n == 0) return s;
-    return HTS_ERR_UNSUPPORTED;
+    if (mode != HTS_GEMM_FP64) return HTS_ERR_UNSUPPORTED;
+    if (n <= 2) {
+        // a 1 x 1 or 2 x 2 pencil is in HT form once B is triangular: stage 0 alone
+        size_t need = 0;
+        hts_workspace_size(n, r, p, &need);
+        if (!work || (reinterpret_cast<uintptr_t>(work) & 255u) || work_bytes < need) return HTS_ERR_WORKSPACE;
+        DeviceGuard g(ctx->device);
+        if (!g.ok) return HTS_ERR_CUDA;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (compq == HTS_COMP_INIT && launch_set_identity(Q, ldq, n, st) != cudaSuccess) return HTS_ERR_CUDA;
+        if (compz == HTS_COMP_INIT && launch_set_identity(Z, ldz, n, st) != cudaSuccess) return HTS_ERR_CUDA;
+        if (run_stage0(n, A, lda, B, ldb, compq == HTS_COMP_NONE ? nullptr : Q, ldq, work, r, stage1_p(p, r),
+                       st) != cudaSuccess)
+            return HTS_ERR_CUDA;
+        return HTS_OK;
+    }
+    if ((s = check_stage1_args(ctx, n, r, p, work, work_bytes)) != HTS_OK) return s;
+    if (r > kMaxR) return HTS_ERR_UNSUPPORTED;
+    int q = (p && p->q > 0) ? p->q : r;
+    if (q > r) return HTS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return HTS_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double *Qp = compq == HTS_COMP_NONE ? nullptr : Q;
+    double *Zp = compz == HTS_COMP_NONE ? nullptr : Z;
+    {
+        ProfScope ps(ctx, st);
+        if (compq == HTS_COMP_INIT && launch_set_identity(Q, ldq, n, st) != cudaSuccess) return HTS_ERR_CUDA;
+        if (compz == HTS_COMP_INIT && launch_set_identity(Z, ldz, n, st) != cudaSuccess) return HTS_ERR_CUDA;
+        if (run_stage0(n, A, lda, B, ldb, Qp, ldq, work, r, stage1_p(p, r), st) != cudaSuccess) return HTS_ERR_CUDA;
+        if (run_stage1(n, r, stage1_p(p, r), A, lda, B, ldb, Qp, ldq, Zp, ldz, work, st) != cudaSuccess)
+            return HTS_ERR_CUDA;
+        ps.done(HTS_K_STAGE1, 0.0, 0.0);
+    }
+    return run_stage2(ctx, n, r, A, lda, B, ldb, Qp, ldq, Zp, ldz, q, p ? p->flags : 0, work, st);
 }
 
 hts_status hts_sync_status(hts_ctx *ctx, void *stream, int info[4])

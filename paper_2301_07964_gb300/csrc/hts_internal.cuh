@@ -215,6 +215,14 @@ cudaError_t launch_s2_apply_left(const LeftArgs &a, cudaStream_t st);
 cudaError_t launch_set_identity(double *M, int ld, int n, cudaStream_t st);
 cudaError_t launch_zero_below(double *M, int ld, int n, int band, cudaStream_t st);
 
+// Stages 0 and 1 (stage01.cu) and workspace sizes.
+size_t stage01_workspace_bytes(int n, int r, int p);
+size_t stage2_workspace_bytes(int n, int r);
+cudaError_t run_stage0(int n, double *A, int lda, double *B, int ldb, double *Q, int ldq, void *work, int r, int p,
+                       cudaStream_t st);
+cudaError_t run_stage1(int n, int nb, int p, double *A, int lda, double *B, int ldb, double *Q, int ldq,
+                       double *Z, int ldz, void *work, cudaStream_t st);
+
 // Same reflector as warp_larfg with one reciprocal square root and one reciprocal on the
 // dependent path: with rs = 1/||x||, beta = -sign(alpha) ||x||, tau = 1 + |alpha| rs and
 // v_i = x_i sign(alpha) rs / tau.  Falls back to the scaled form when the sum of squares

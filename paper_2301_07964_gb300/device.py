@@ -66,6 +66,29 @@ class Reducer:
             raise b.HTSError(st, "hts_reduce_stage2")
         return st
 
+    def _call(self, fn, name, A, B, r, Q, Z, compq, compz, q, p, flags, mode, stream, check):
+        n = A.shape[0]
+        params = b.hts_params(q=q, p=p, flags=flags)
+        work = self.workspace(n, r, params)
+        if Q is None:
+            compq = b.HTS_COMP_NONE
+        if Z is None:
+            compz = b.HTS_COMP_NONE
+        st = fn(self.ctx, n, r, A, _ld(A), B, _ld(B), compq, Q, _ld(Q), compz, Z, _ld(Z), mode, params, work,
+                work.numel(), stream)
+        if check and st != b.HTS_OK:
+            raise b.HTSError(st, name)
+        return st
+
+    def stage1(self, A, B, r, Q=None, Z=None, compq=b.HTS_COMP_UPDATE, compz=b.HTS_COMP_UPDATE, p=0, flags=0,
+               mode=b.HTS_GEMM_FP64, stream=None, check=True) -> int:
+        return self._call(b.hts_reduce_stage1, "hts_reduce_stage1", A, B, r, Q, Z, compq, compz, 0, p, flags,
+                          mode, stream, check)
+
+    def reduce(self, A, B, r, Q=None, Z=None, compq=b.HTS_COMP_UPDATE, compz=b.HTS_COMP_UPDATE, q=0, p=0,
+               flags=0, mode=b.HTS_GEMM_FP64, stream=None, check=True) -> int:
+        return self._call(b.hts_reduce, "hts_reduce", A, B, r, Q, Z, compq, compz, q, p, flags, mode, stream, check)
+
     def sync_status(self, stream=None):
         return b.hts_sync_status(self.ctx, stream)
 
