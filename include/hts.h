@@ -159,6 +159,25 @@ hts_status hts_reduce(hts_ctx *ctx, int n, int r,
                       void *work, size_t work_bytes, void *stream);
 
 /*
+ * Batched full reduction (QR of B, stage 1 with n_b = r_i, stage 2) of `count` independent
+ * pencils of possibly different sizes in one launch.  The array arguments are host arrays
+ * of length count (device pointers for the matrices); compq / compz apply to every pencil.
+ * Each pencil is reduced by one thread block with its reflectors applied one at a time, so
+ * the batch, not a single pencil, supplies the parallelism; blocks start largest pencil
+ * first.  Limits of this path: n_i <= 512, r_i <= 16 and r_i < n_i (or n_i <= 2),
+ * p * r_i <= 64 (p defaults to min(8, 64/r_i)).  `work` holds the pencil descriptors:
+ * hts_workspace_size_batched() bytes.  The results equal those of hts_reduce up to rounding.
+ */
+hts_status hts_workspace_size_batched(int count, const int *n, const int *r, const hts_params *p,
+                                      size_t *bytes);
+hts_status hts_reduce_batched(hts_ctx *ctx, int count, const int *n, const int *r,
+                              double *const *A, const int *lda, double *const *B, const int *ldb,
+                              hts_comp compq, double *const *Q, const int *ldq,
+                              hts_comp compz, double *const *Z, const int *ldz,
+                              hts_gemm_mode mode, const hts_params *p, void *work, size_t work_bytes,
+                              void *stream);
+
+/*
  * Wait for `stream`, then report and clear the context's device status word.
  * info (may be NULL) receives {pencil, group, k, j} of the first device-side error.
  * Returns HTS_OK, HTS_ERR_TIMEOUT, or HTS_ERR_CUDA if the stream itself failed.

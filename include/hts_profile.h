@@ -21,6 +21,7 @@ enum {
     HTS_K_UTIL = 3,         /* identity initialisation, final zeroing */
     HTS_K_STAGE1 = 4,       /* stage 0 / stage 1 kernels */
     HTS_K_APPLY_QZ = 5,     /* delayed right updates of Q and Z (stage 2, side stream) */
+    HTS_K_BATCH = 6,        /* batched reduction of many small pencils */
     HTS_K_NKINDS = 8
 };
 

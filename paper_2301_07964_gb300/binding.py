@@ -40,7 +40,7 @@ class hts_params(ctypes.Structure):
 
 HTS_K_NKINDS = 8
 KERNEL_KINDS = {0: "k_s2_generate", 1: "k_s2_apply_right", 2: "k_s2_apply_left", 3: "util", 4: "stage1",
-                5: "k_s2_apply_right_qz"}
+                5: "k_s2_apply_right_qz", 6: "k_reduce_batched"}
 
 
 class hts_kernel_profile(ctypes.Structure):
@@ -82,6 +82,13 @@ def load(path: str = LIB_PATH):
         f.restype = _I
     lib.hts_reduce_stage2_noalloc.argtypes = _RED_ARGS[:15] + [_VP]
     lib.hts_reduce_stage2_noalloc.restype = _I
+    IP = ctypes.POINTER(ctypes.c_int)
+    PP = ctypes.POINTER(_VP)
+    lib.hts_workspace_size_batched.argtypes = [_I, IP, IP, ctypes.POINTER(hts_params), ctypes.POINTER(ctypes.c_size_t)]
+    lib.hts_workspace_size_batched.restype = _I
+    lib.hts_reduce_batched.argtypes = [_VP, _I, IP, IP, PP, IP, PP, IP, _I, PP, IP, _I, PP, IP, _I,
+                                       ctypes.POINTER(hts_params), _VP, ctypes.c_size_t, _VP]
+    lib.hts_reduce_batched.restype = _I
     lib.hts_sync_status.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int)]
     lib.hts_sync_status.restype = _I
     lib.hts_status_string.argtypes = [_I]
@@ -185,6 +192,34 @@ def hts_reduce(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode, pa
                work_bytes, stream=None) -> int:
     return _reduce("hts_reduce", ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode,
                    params, work, work_bytes, stream)
+
+
+def _iarr(vals):
+    return (ctypes.c_int * max(1, len(vals)))(*[int(v) for v in vals])
+
+
+def _parr(vals):
+    return (_VP * max(1, len(vals)))(*[_ptr(v) for v in vals])
+
+
+def hts_workspace_size_batched(n, r, params=None) -> int:
+    out = ctypes.c_size_t(0)
+    st = load().hts_workspace_size_batched(len(n), _iarr(n), _iarr(r), _params(params), ctypes.byref(out))
+    if st != HTS_OK:
+        raise HTSError(st, "hts_workspace_size_batched")
+    return out.value
+
+
+def hts_reduce_batched(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode, params, work, work_bytes,
+                       stream=None) -> int:
+    """Lists of length count: sizes, r, matrices (device pointers or tensors) and leading dimensions."""
+    count = len(n)
+    Qs = Q if Q is not None else [None] * count
+    Zs = Z if Z is not None else [None] * count
+    return load().hts_reduce_batched(ctx, count, _iarr(n), _iarr(r), _parr(A), _iarr(lda), _parr(B), _iarr(ldb),
+                                     int(compq), _parr(Qs), _iarr(ldq if ldq is not None else [1] * count),
+                                     int(compz), _parr(Zs), _iarr(ldz if ldz is not None else [1] * count),
+                                     int(mode), _params(params), _ptr(work), int(work_bytes), _stream(stream))
 
 
 def hts_sync_status(ctx, stream=None):

@@ -1,0 +1,295 @@
+// Batched reduction of many small pencils in one launch (hts_reduce_batched).
+//
+// One thread block reduces one whole pencil: QR of B (stage 0), Alg. 1 with n_b = r (stage
+// 1) and Alg. 2 (stage 2).  Every reflector is applied on its own, in the order the
+// algorithms state, with the work of each application spread over the block (one warp per
+// column for left applications, one thread per row for right applications).  Blocks are
+// launched largest pencil first, so the hardware's in-order block dispatch gives a
+// longest-processing-time schedule; many small pencils keep every SM busy.
+#include "hts_internal.cuh"
+
+namespace hts {
+
+namespace {
+
+constexpr int kBT = 256;            // threads per pencil
+constexpr int kBW = kBT / 32;
+constexpr int kBatchMaxN = 512;     // reflector buffer length (largest pencil)
+constexpr int kBatchMaxBlk = 64;    // largest B block (p * r) of stage 1 kept in shared memory
+
+struct BatchShared {
+    double v[kBatchMaxN];                        // current reflector (explicit v_0 = 1)
+    double W[kBatchMaxBlk * (kBatchMaxBlk + 1)];  // B block for the RQ (row-major)
+    double Mq[16 * (kBatchMaxBlk + 1)];          // first rows of the RQ's orthogonal factor
+    double rqt[kBatchMaxBlk];
+    double red[kBW];
+    double tau, beta, scale;
+};
+
+__device__ __forceinline__ double bsum(double x, BatchShared &S)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    x = warp_sum(x);
+    __syncthreads();
+    if (lane == 0) S.red[warp] = x;
+    __syncthreads();
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kBW; ++w) s += S.red[w];
+    return s;
+}
+
+// Reflector (dlarfg convention) from m entries x[0], x[inc], ...; v goes to S.v (v_0 = 1),
+// tau / beta to S.tau / S.beta; x is overwritten by (beta, 0, ..., 0).
+__device__ void blk_larfg(double *x, long inc, int m, BatchShared &S)
+{
+    double part = 0.0;
+    for (int i = 1 + threadIdx.x; i < m; i += kBT) part += x[i * inc] * x[i * inc];
+    const double ssq = bsum(part, S);
+    if (threadIdx.x == 0) {
+        const double alpha = x[0];
+        if (m <= 1 || ssq == 0.0) {
+            S.tau = 0.0; S.beta = alpha; S.scale = 0.0;
+        } else {
+            const double nrm = sqrt(alpha * alpha + ssq);
+            const double b = alpha >= 0.0 ? -nrm : nrm;
+            S.tau = (b - alpha) / b;
+            S.scale = 1.0 / (alpha - b);
+            S.beta = b;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += kBT) {
+        S.v[i] = (i == 0) ? 1.0 : x[i * inc] * S.scale;
+        x[i * inc] = (i == 0) ? S.beta : 0.0;
+    }
+    __syncthreads();
+}
+
+// M(r0:r0+m-1, c0:c1) := H M(...), one warp per column
+__device__ void blk_left(double *M, int ld, int r0, int m, int c0, int c1, const BatchShared &S)
+{
+    const double tau = S.tau;
+    if (tau == 0.0 || c1 < c0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = c0 + warp; c <= c1; c += kBW) {
+        double *col = M + AT(ld, r0, c);
+        double d = 0.0;
+        for (int i = lane; i < m; i += 32) d += S.v[i] * col[i];
+        d = warp_sum(d) * tau;
+        for (int i = lane; i < m; i += 32) col[i] -= d * S.v[i];
+    }
+}
+
+// M(x0:x1, c0:c0+m-1) := M(...) H, one thread per row
+__device__ void blk_right(double *M, int ld, int x0, int x1, int c0, int m, const BatchShared &S)
+{
+    const double tau = S.tau;
+    if (tau == 0.0) return;
+    for (int x = x0 + threadIdx.x; x <= x1; x += kBT) {
+        double *row = M + AT(ld, x, c0);
+        double d0 = 0.0, d1 = 0.0;
+        int i = 0;
+        for (; i + 1 < m; i += 2) {
+            d0 += row[(size_t)i * ld] * S.v[i];
+            d1 += row[(size_t)(i + 1) * ld] * S.v[i + 1];
+        }
+        if (i < m) d0 += row[(size_t)i * ld] * S.v[i];
+        const double d = (d0 + d1) * tau;
+        for (int c = 0; c < m; ++c) row[(size_t)c * ld] -= d * S.v[c];
+    }
+}
+
+// RQ of the m x m block already in S.W (row-major, ld m+1), last row first; reflectors kept in
+// the zeroed part of S.W, taus in S.rqt.  Then S.Mq (l x m) = first l rows of Q~.
+__device__ void blk_rq_first_rows(int m, int l, BatchShared &S)
+{
+    const int ldw = m + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int s = m - 1; s >= 1; --s) {
+        double part = 0.0;
+        for (int c = threadIdx.x; c < s; c += kBT) part += S.W[s * ldw + c] * S.W[s * ldw + c];
+        const double ssq = bsum(part, S);
+        if (threadIdx.x == 0) {
+            const double alpha = S.W[s * ldw + s];
+            if (ssq == 0.0) {
+                S.tau = 0.0; S.beta = alpha; S.scale = 0.0;
+            } else {
+                const double nrm = sqrt(alpha * alpha + ssq);
+                const double b = alpha >= 0.0 ? -nrm : nrm;
+                S.tau = (b - alpha) / b; S.scale = 1.0 / (alpha - b); S.beta = b;
+            }
+            S.rqt[s] = S.tau;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < s; c += kBT) S.W[s * ldw + c] *= S.scale;
+        __syncthreads();
+        const double ts = S.rqt[s];
+        if (ts != 0.0) {
+            for (int row = warp; row < s; row += kBW) {
+                double d = 0.0;
+                for (int c = lane; c <= s; c += 32) d += S.W[row * ldw + c] * (c == s ? 1.0 : S.W[s * ldw + c]);
+                d = warp_sum(d) * ts;
+                for (int c = lane; c <= s; c += 32) S.W[row * ldw + c] -= d * (c == s ? 1.0 : S.W[s * ldw + c]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < l * m; e += kBT) S.Mq[(e / m) * ldw + e % m] = (e / m == e % m) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int s = 1; s <= m - 1; ++s) {
+        const double ts = S.rqt[s];
+        if (ts != 0.0) {
+            for (int t = warp; t < l; t += kBW) {
+                double d = 0.0;
+                for (int c = lane; c <= s; c += 32) d += S.Mq[t * ldw + c] * (c == s ? 1.0 : S.W[s * ldw + c]);
+                d = warp_sum(d) * ts;
+                for (int c = lane; c <= s; c += 32) S.Mq[t * ldw + c] -= d * (c == s ? 1.0 : S.W[s * ldw + c]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__device__ void load_block(const double *B, int ldb, int i1, int m, BatchShared &S)
+{
+    for (int e = threadIdx.x; e < m * m; e += kBT) {
+        const int i = e % m, c = e / m;
+        S.W[i * (m + 1) + c] = B[AT(ldb, i1 + i, i1 + c)];
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+struct BatchDesc {
+    double *A, *B, *Q, *Z;
+    int n, r, lda, ldb, ldq, ldz;
+};
+
+__global__ void __launch_bounds__(kBT) k_reduce_batched(const BatchDesc *desc, const int *order, int p_param,
+                                                         int compq, int compz, const int *status)
+{
+    __shared__ BatchShared S;
+    const BatchDesc d = desc[order[blockIdx.x]];
+    const int n = d.n, r = d.r;
+    double *A = d.A, *B = d.B;
+    double *Q = compq ? d.Q : nullptr, *Z = compz ? d.Z : nullptr;
+    if (__ldcg(status) != 0) return;
+    // identity initialisation
+    for (int e = threadIdx.x; e < n * n; e += kBT) {
+        const int i = e % n + 1, c = e / n + 1;
+        if (compq == HTS_COMP_INIT) Q[AT(d.ldq, i, c)] = (i == c) ? 1.0 : 0.0;
+        if (compz == HTS_COMP_INIT) Z[AT(d.ldz, i, c)] = (i == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+
+    // ---- stage 0: QR of B
+    for (int j = 1; j <= n - 1; ++j) {
+        const int m = n - j + 1;
+        blk_larfg(B + AT(d.ldb, j, j), 1, m, S);
+        blk_left(B, d.ldb, j, m, j + 1, n, S);
+        blk_left(A, d.lda, j, m, 1, n, S);
+        if (Q) blk_right(Q, d.ldq, 1, n, j, m, S);
+        __syncthreads();
+    }
+    if (n <= 2) return;
+
+    // ---- stage 1: Alg. 1 with n_b = r
+    const int nb = r;
+    const int p = (p_param > 0) ? p_param : imin(8, imax(2, kBatchMaxBlk / nb));
+    for (int j = 1; j <= n - 2; j += nb) {
+        const int j1 = j, j2 = imin(n, j + nb - 1);
+        const int num = n - nb - j + 1, den = (p - 1) * nb;
+        const int nblocks = num > 0 ? (num + den - 1) / den : 0;
+        for (int k = nblocks - 1; k >= 0; --k) {
+            const int i1 = j + nb + k * (p - 1) * nb;
+            const int i2 = imin(n, i1 + p * nb - 1);
+            for (int c = j1; c <= j2; ++c) {
+                const int rs = i1 + (c - j1);
+                if (rs > i2) break;
+                const int m = i2 - rs + 1;
+                blk_larfg(A + AT(d.lda, rs, c), 1, m, S);
+                blk_left(A, d.lda, rs, m, c + 1, n, S);
+                blk_left(B, d.ldb, rs, m, i1, n, S);
+                if (Q) blk_right(Q, d.ldq, 1, n, rs, m, S);
+                __syncthreads();
+            }
+        }
+        for (int k = nblocks - 1; k >= 0; --k) {
+            const int i1 = j + nb + k * (p - 1) * nb;
+            const int i2 = imin(n, i1 + p * nb - 1);
+            const int m = i2 - i1 + 1, l = imin(nb, m);
+            load_block(B, d.ldb, i1, m, S);
+            blk_rq_first_rows(m, l, S);
+            for (int t = 0; t < l; ++t) {
+                const int len = m - t;
+                blk_larfg(&S.Mq[t * (m + 1) + t], 1, len, S);
+                // the remaining rows of Mq
+                if (S.tau != 0.0) {
+                    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                    for (int row = t + 1 + warp; row < l; row += kBW) {
+                        double dd = 0.0;
+                        for (int c = lane; c < len; c += 32) dd += S.Mq[row * (m + 1) + t + c] * S.v[c];
+                        dd = warp_sum(dd) * S.tau;
+                        for (int c = lane; c < len; c += 32) S.Mq[row * (m + 1) + t + c] -= dd * S.v[c];
+                    }
+                }
+                blk_right(A, d.lda, 1, n, i1 + t, len, S);
+                blk_right(B, d.ldb, 1, i2, i1 + t, len, S);
+                if (Z) blk_right(Z, d.ldz, 1, n, i1 + t, len, S);
+                __syncthreads();
+                for (int x = i1 + t + 1 + threadIdx.x; x <= i2; x += kBT) B[AT(d.ldb, x, i1 + t)] = 0.0;
+                __syncthreads();
+            }
+        }
+    }
+
+    // ---- stage 2: Alg. 2
+    for (int j = 1; j <= n - 2 && r > 1; ++j) {
+        const int nblocks = 1 + (n - j - 2) / r;
+        for (int k = 0; k < nblocks; ++k) {
+            const int jb = j + imax(0, (k - 1) * r + 1);
+            const int i1 = j + k * r + 1;
+            const int i2 = imin(j + (k + 1) * r, n);
+            const int i3 = imin(j + (k + 2) * r, n);
+            const int m = i2 - i1 + 1;
+            blk_larfg(A + AT(d.lda, i1, jb), 1, m, S);
+            blk_left(A, d.lda, i1, m, jb + 1, n, S);
+            blk_left(B, d.ldb, i1, m, i1, n, S);
+            if (Q) blk_right(Q, d.ldq, 1, n, i1, m, S);
+            __syncthreads();
+            load_block(B, d.ldb, i1, m, S);
+            blk_rq_first_rows(m, 1, S);
+            blk_larfg(&S.Mq[0], 1, m, S);
+            blk_right(A, d.lda, 1, i3, i1, m, S);
+            blk_right(B, d.ldb, 1, i2, i1, m, S);
+            if (Z) blk_right(Z, d.ldz, 1, n, i1, m, S);
+            __syncthreads();
+            for (int x = i1 + 1 + threadIdx.x; x <= i2; x += kBT) B[AT(d.ldb, x, i1)] = 0.0;
+            __syncthreads();
+        }
+    }
+}
+
+cudaError_t launch_reduce_batched(const void *desc, const int *order, int count, int p, int compq, int compz,
+                                  const int *status, cudaStream_t st)
+{
+    k_reduce_batched<<<count, kBT, 0, st>>>(static_cast<const BatchDesc *>(desc), order, p, compq, compz, status);
+    return cudaGetLastError();
+}
+
+size_t batch_desc_bytes() { return sizeof(BatchDesc); }
+
+void fill_batch_desc(void *dst, int i, double *A, double *B, double *Q, double *Z, int n, int r, int lda, int ldb,
+                     int ldq, int ldz)
+{
+    BatchDesc *d = static_cast<BatchDesc *>(dst) + i;
+    d->A = A; d->B = B; d->Q = Q; d->Z = Z;
+    d->n = n; d->r = r; d->lda = lda; d->ldb = ldb; d->ldq = ldq; d->ldz = ldz;
+}
+
+int batch_max_n() { return kBatchMaxN; }
+int batch_max_block() { return kBatchMaxBlk; }
+
+}  // namespace hts

@@ -215,6 +215,16 @@ cudaError_t launch_s2_apply_left(const LeftArgs &a, cudaStream_t st);
 cudaError_t launch_set_identity(double *M, int ld, int n, cudaStream_t st);
 cudaError_t launch_zero_below(double *M, int ld, int n, int band, cudaStream_t st);
 
+// Batched reduction (batch.cu).
+struct BatchDesc;
+cudaError_t launch_reduce_batched(const void *desc, const int *order, int count, int p, int compq, int compz,
+                                  const int *status, cudaStream_t st);
+size_t batch_desc_bytes();
+void fill_batch_desc(void *dst, int i, double *A, double *B, double *Q, double *Z, int n, int r, int lda, int ldb,
+                     int ldq, int ldz);
+int batch_max_n();
+int batch_max_block();
+
 // Stages 0 and 1 (stage01.cu) and workspace sizes.
 size_t stage01_workspace_bytes(int n, int r, int p);
 size_t stage2_workspace_bytes(int n, int r);
