@@ -396,6 +396,121 @@ def run_ours(args, n, r):
     return 0
 
 
+# ---------------------------------------------------------------------------------------
+# supplementary workloads (not the metric line): full reduction and the batch configuration
+# ---------------------------------------------------------------------------------------
+def run_reduce(args, n, r):
+    """Full reduction (QR of B, stage 1, stage 2) of a dense pencil with A, B iid N(0, 1)."""
+    import torch
+    from paper_2301_07964_gb300 import binding as b
+    from paper_2301_07964_gb300 import build
+    from paper_2301_07964_gb300.device import Reducer, colmajor_empty, to_device
+    from paper_2301_07964_gb300.inputs import ill_conditioned_pencil, random_pencil
+    build.build()
+    b.load()
+    seed = args.seed if args.seed is not None else 2
+    if args.ill:
+        A, B = ill_conditioned_pencil(n, seed)
+    else:
+        A, B = random_pencil(n, seed)
+    dA0, dB0 = to_device(A), to_device(B)
+    dA, dB, dQ, dZ = (colmajor_empty(n) for _ in range(4))
+    red = Reducer(0)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        dA.copy_(dA0)
+        dB.copy_(dB0)
+        red.reduce(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=args.q, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    b.hts_profile_begin(red.ctx, 8 * n + 64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof, _ = b.hts_profile_end(red.ctx)
+    st, info = red.sync_status()
+    assert st == b.HTS_OK, info
+    ms = e0.elapsed_time(e1) / args.steps
+    I = torch.eye(n, dtype=torch.float64, device="cuda")
+    bwd = {"A": float(torch.linalg.norm(dQ @ dA @ dZ.T - dA0) / torch.linalg.norm(dA0)),
+           "B": float(torch.linalg.norm(dQ @ dB @ dZ.T - dB0) / torch.linalg.norm(dB0)),
+           "orth_Q": float(torch.linalg.norm(dQ.T @ dQ - I) / n ** 0.5),
+           "orth_Z": float(torch.linalg.norm(dZ.T @ dZ - I) / n ** 0.5)}
+    s01 = prof.get("stage1", {}).get("ms", 0.0) / args.steps
+    print(json.dumps({"workload": "full reduction n=%d r=%d%s" % (n, r, " ill-conditioned B" if args.ill else ""),
+                      "ms_per_step": ms, "stage01_ms": s01, "stage2_ms": ms - s01,
+                      "gflops_two_stage_21.33n3": 21.33 * n ** 3 / (ms / 1e3) / 1e9,
+                      "gflops_stage2_10n3": paper_flops(n) / ((ms - s01) / 1e3) / 1e9,
+                      "backward_error": bwd, "steps": args.steps,
+                      "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches": v["launches"] // args.steps}
+                                  for k, v in prof.items()}}))
+    red.close()
+    return 0
+
+
+def run_batch(args):
+    """4096 pencils, n uniform in [32, 512], r = min(8, n // 8), A, B iid N(0, 1), full
+    reduction with Q and Z in one hts_reduce_batched launch."""
+    import torch
+    from paper_2301_07964_gb300 import binding as b
+    from paper_2301_07964_gb300 import build
+    from paper_2301_07964_gb300.device import Reducer, colmajor_empty
+    from paper_2301_07964_gb300.inputs import batch_sizes
+    build.build()
+    b.load()
+    count = args.count
+    ns, rs = batch_sizes(count, 5)
+    ns, rs = [int(x) for x in ns], [int(x) for x in rs]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    A0 = [torch.randn(n, n, dtype=torch.float64, device="cuda", generator=gen).t() for n in ns]
+    B0 = [torch.randn(n, n, dtype=torch.float64, device="cuda", generator=gen).t() for n in ns]
+    dA = [colmajor_empty(n) for n in ns]
+    dB = [colmajor_empty(n) for n in ns]
+    dQ = [colmajor_empty(n) for n in ns]
+    dZ = [colmajor_empty(n) for n in ns]
+    red = Reducer(0)
+    nbytes = b.hts_workspace_size_batched(ns, rs)
+    work = torch.empty(max(256, nbytes), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def restore():
+        for x, y in zip(dA, A0):
+            x.copy_(y)
+        for x, y in zip(dB, B0):
+            x.copy_(y)
+
+    times = []
+    for it in range(args.warmup + args.steps):
+        restore()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = b.hts_reduce_batched(red.ctx, ns, rs, dA, ns, dB, ns, b.HTS_COMP_INIT, dQ, ns, b.HTS_COMP_INIT, dZ, ns,
+                                  b.HTS_GEMM_FP64, None, work, work.numel(), stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert st == b.HTS_OK
+        if it >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    st, info = red.sync_status()
+    assert st == b.HTS_OK, info
+    ms = sum(times) / len(times)
+    flops = sum(21.33 * n ** 3 for n in ns)
+    print(json.dumps({"workload": "batch of %d pencils, n uniform in [32, 512], r = min(8, n // 8), full "
+                                  "reduction with Q, Z, one launch" % count,
+                      "ms_per_batch": ms, "pencils_per_s": count / (ms / 1e3),
+                      "gflops_two_stage_21.33n3": flops / (ms / 1e3) / 1e9, "steps": args.steps}))
+    red.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,7 +526,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-sweeps", type=int, default=24)
+    ap.add_argument("--workload", choices=["stage2", "reduce", "batch"], default="stage2")
+    ap.add_argument("--ill", action="store_true", help="reduce: ill-conditioned B")
+    ap.add_argument("--seed", type=int, default=None)
+    ap.add_argument("--count", type=int, default=4096)
     args = ap.parse_args()
+    if args.workload == "reduce":
+        return run_reduce(args, args.n, args.r)
+    if args.workload == "batch":
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args, args.n, args.r)
     return run_ours(args, args.n, args.r)

@@ -7,6 +7,13 @@
 // a wavefront three blocks apart, synchronised through one progress word per sweep (release /
 // acquire at GPU scope, waits bounded in time).
 //
+// Each sweep also has a helper block.  A step's band update covers rows i4 .. i3; only the
+// rows from cr = j1 + k r + 1 down are ever read by a later step of the group (pivot columns,
+// B blocks); the rows above exist to keep the group's reflectors in order for the delayed
+// updates.  The main block updates rows >= cr and publishes; the helper block then updates
+// rows i4 .. cr-1 and publishes its own progress, on which the next sweep waits (block k+1 of
+// the helper before step k).
+//
 // One step, in native FP64:
 //   1. prefetch: pivot column segment A(rlo:rhi, jb), the block's newest B column, the earlier
 //      sweeps' left reflectors of block k and the rest of the B block (one memory round trip);
@@ -15,7 +22,8 @@
 //   4. B block := Q^ B block;
 //   5. RQ of the B block, last row first, accumulating the right factor G (W G = R~);
 //   6. opposite reflector Z^_k^j mapping the first row of Q~ = G(:, 1)^T to beta e_1;
-//   7. band update A(i4:i3, i1:i2) Z^, B(i4:i2, i1:i2) Z^, with B(i1+1:i2, i1) = 0 exactly;
+//   7. band update A(cr:i3, i1:i2) Z^, B(cr:i2, i1:i2) Z^, with B(i1+1:i2, i1) = 0 exactly
+//      (rows i4 .. cr-1 by the helper block);
 //   8. publish block k of sweep j.
 // Block-level updates use groups of 8 lanes per row or column (3-level reductions), so one
 // round covers up to 32 rows.
@@ -38,6 +46,53 @@ __device__ __forceinline__ double grp_sum(double v)
     return v;
 }
 
+// Bounded wait (one thread) until *flag >= need; on expiry records HTS_ERR_TIMEOUT.
+__device__ bool wait_at_least(const unsigned long long *flag, unsigned long long need, int *status, int group, int k,
+                              int j)
+{
+    const unsigned long long t0 = globaltimer_ns();
+    long long polls = 0;
+    while (ld_acquire_u64(flag) < need) {
+        if (++polls > kSpinLimit || globaltimer_ns() - t0 > kWaitLimitNs) {
+            record_error(status, HTS_ERR_TIMEOUT, 0, group, k, j);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Rows x0 .. x0+na-1 of A and x0 .. x0+nbr-1 of B, columns i1 .. i1+m-1, times Z^ = I - tz v v^T
+// (one thread per row).  zero_first: B(x, i1) := 0 exactly for x > i1 (the reduced column).
+__device__ void band_rows(double *A, int lda, double *B, int ldb, int x0, int na, int nbr, int i1, int m, double tz,
+                          const double *vv, bool zero_first)
+{
+    for (int t = threadIdx.x; t < na + nbr; t += kGenThreads) {
+        const bool isA = t < na;
+        const int x = x0 + (isA ? t : t - na);
+        double *base = isA ? A : B;
+        const int ld = isA ? lda : ldb;
+        double rowv[kMaxR];
+        double d0 = 0.0, d1 = 0.0;
+#pragma unroll
+        for (int c = 0; c < kMaxR; ++c) {
+            if (c < m) {
+                rowv[c] = __ldcg(base + AT(ld, x, i1 + c));
+                if (c & 1) d1 += rowv[c] * vv[c];
+                else d0 += rowv[c] * vv[c];
+            }
+        }
+        const double d = (d0 + d1) * tz;
+#pragma unroll
+        for (int c = 0; c < kMaxR; ++c) {
+            if (c < m) {
+                double val = rowv[c] - d * vv[c];
+                if (zero_first && !isA && c == 0 && x > i1) val = 0.0;
+                base[AT(ld, x, i1 + c)] = val;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(kGenThreads) k_s2_generate(GenArgs a)
@@ -52,7 +107,8 @@ __global__ void __launch_bounds__(kGenThreads) k_s2_generate(GenArgs a)
     __shared__ double s_tau;
     __shared__ int s_abort;
 
-    const int s = blockIdx.x;
+    const bool helper = (int)blockIdx.x >= a.qg;
+    const int s = helper ? (int)blockIdx.x - a.qg : (int)blockIdx.x;
     const int j = a.j1 + s;
     const int n = a.n, r = a.r, j1 = a.j1, qg = a.qg;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -69,28 +125,52 @@ __global__ void __launch_bounds__(kGenThreads) k_s2_generate(GenArgs a)
     const int lda = a.lda, ldb = a.ldb;
     const int nlazy = j - j1;
 
-    for (int k = kg + tid; k < kdim; k += kGenThreads) {   // blocks this sweep does not reach
+    for (int k = kg + tid; !helper && k < kdim; k += kGenThreads) {   // blocks this sweep does not reach
         TQs[k] = 0.0;
         TZs[k] = 0.0;
     }
-    if (tid == 0) s_abort = __ldcg(a.status) != 0;
+    if (tid == 0) s_abort = __ldcg(a.status) != 0;   // an earlier kernel of this call failed
     __syncthreads();
     if (s_abort) return;
+    unsigned long long *hflags = a.flags + a.qmax;       // progress of the helper blocks
+
+    if (helper) {
+        // Band rows above the critical rows of each step: rows i4 .. cr-1, where cr = j1+kr+1
+        // is the first row of block k that any step reads.  They only carry the ordering of
+        // the group's reflectors, so they are updated here, behind the main block.
+        for (int k = 0; k < kg; ++k) {
+            if (tid == 0) {
+                const bool ok = wait_at_least(a.flags + s, a.epoch | (unsigned long long)(k + 1), a.status, a.group, k, j) &&
+                                (s == 0 || wait_at_least(hflags + s - 1, a.epoch | (unsigned long long)(k + 2), a.status,
+                                                         a.group, k, j));
+                s_abort = !ok;
+            }
+            __syncthreads();
+            if (s_abort) return;
+            const StepGeom g = step_geom(n, r, j1, qg, k, j);
+            const int m = g.i2 - g.i1 + 1;
+            const int cr = j1 + k * r + 1;
+            const double tz = __ldcg(TZs + k);
+            if (tid < kMaxR) vv[tid] = tid < m ? __ldcg(VZs + (size_t)k * r + tid) : 0.0;
+            __syncthreads();
+            const int na = imax(0, imin(cr - 1, g.i3) - g.i4 + 1), nbr = imax(0, imin(cr - 1, g.i2) - g.i4 + 1);
+            if (tz != 0.0) band_rows(A, lda, B, ldb, g.i4, na, nbr, g.i1, m, tz, vv, false);
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) st_release_u64(hflags + s, a.epoch | (unsigned long long)(k + 1));
+        }
+        if (tid == 0) st_release_u64(hflags + s, a.epoch | 0xffffffffULL);
+        return;
+    }
 
     for (int k = 0; k < kl; ++k) {
-        // ---- wait until sweep j-1 has finished block k+2 (or all of its blocks)
-        if (tid == 0 && s > 0) {
-            const unsigned long long need = a.epoch | (unsigned long long)imin(k + 3, kl_prev);
-            const unsigned long long t0 = globaltimer_ns();
-            long long polls = 0;
-            while (ld_acquire_u64(a.flags + s - 1) < need) {
-                if (++polls > kSpinLimit || globaltimer_ns() - t0 > kWaitLimitNs) {
-                    record_error(a.status, HTS_ERR_TIMEOUT, 0, a.group, k, j);
-                    s_abort = 1;
-                    break;
-                }
-            }
-        }
+        // ---- wait until sweep j-1 has finished block k+2 (or all of its blocks), and its helper
+        //      block k+1: the helper's rows of block k+1 include the upper rows of this step's
+        //      newest B column (read by the prefetch) and share column i2 with this step's band
+        if (tid == 0 && s > 0)
+            s_abort = !(wait_at_least(a.flags + s - 1, a.epoch | (unsigned long long)imin(k + 3, kl_prev), a.status,
+                                      a.group, k, j) &&
+                        wait_at_least(hflags + s - 1, a.epoch | (unsigned long long)(k + 2), a.status, a.group, k, j));
         __syncthreads();
         if (s_abort) return;
 
@@ -238,34 +318,12 @@ __global__ void __launch_bounds__(kGenThreads) k_s2_generate(GenArgs a)
             }
             __syncthreads();
 
-            // ---- 7. band updates
+            // ---- 7. band updates of the critical rows (rows >= cr = j1+kr+1; the rows above
+            //      go to the helper block)
             const double tz = s_tau;
-            const int na = imax(0, g.i3 - g.i4 + 1), nbr = imax(0, g.i2 - g.i4 + 1);
-            for (int t = tid; t < na + nbr; t += kGenThreads) {
-                const bool isA = t < na;
-                const int x = g.i4 + (isA ? t : t - na);
-                double *base = isA ? A : B;
-                const int ld = isA ? lda : ldb;
-                double rowv[kMaxR];
-                double d0 = 0.0, d1 = 0.0;
-#pragma unroll
-                for (int c = 0; c < kMaxR; ++c) {
-                    if (c < m) {
-                        rowv[c] = __ldcg(base + AT(ld, x, g.i1 + c));
-                        if (c & 1) d1 += rowv[c] * vv[c];
-                        else d0 += rowv[c] * vv[c];
-                    }
-                }
-                const double d = (d0 + d1) * tz;
-#pragma unroll
-                for (int c = 0; c < kMaxR; ++c) {
-                    if (c < m) {
-                        double val = rowv[c] - d * vv[c];
-                        if (!isA && c == 0 && x > g.i1) val = 0.0;
-                        base[AT(ld, x, g.i1 + c)] = val;
-                    }
-                }
-            }
+            const int x0 = imax(g.i4, j1 + k * r + 1);
+            const int na = imax(0, g.i3 - x0 + 1), nbr = imax(0, g.i2 - x0 + 1);
+            band_rows(A, lda, B, ldb, x0, na, nbr, g.i1, m, tz, vv, true);
         }
 
         // ---- 8. publish block k of this sweep
@@ -279,7 +337,8 @@ __global__ void __launch_bounds__(kGenThreads) k_s2_generate(GenArgs a)
 cudaError_t launch_s2_generate(const GenArgs &a, cudaStream_t st)
 {
     void *args[] = {(void *)&a};
-    return cudaLaunchCooperativeKernel((const void *)k_s2_generate, dim3(a.qg), dim3(kGenThreads), args, 0, st);
+    // qg main blocks (one per sweep) and qg helper blocks
+    return cudaLaunchCooperativeKernel((const void *)k_s2_generate, dim3(2 * a.qg), dim3(kGenThreads), args, 0, st);
 }
 
 }  // namespace hts

@@ -48,7 +48,7 @@ S2Layout s2_layout(int n, int r)
         L.off_vz[b] = o; o = align_up(o + nv, 256);
         L.off_tz[b] = o; o = align_up(o + nt, 256);
     }
-    L.off_flags = o; o = align_up(o + (size_t)L.qmax * sizeof(unsigned long long), 256);
+    L.off_flags = o; o = align_up(o + 2 * (size_t)L.qmax * sizeof(unsigned long long), 256);
     L.total = o;
     return L;
 }
@@ -156,7 +156,7 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         R[b].kdim = L.kdim;
     }
     unsigned long long *fl = reinterpret_cast<unsigned long long *>(w + L.off_flags);
-    cudaError_t e = cudaMemsetAsync(fl, 0, (size_t)L.qmax * sizeof(unsigned long long), st);
+    cudaError_t e = cudaMemsetAsync(fl, 0, 2 * (size_t)L.qmax * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return HTS_ERR_CUDA;
     const bool qz = (Q != nullptr) || (Z != nullptr);
     cudaStream_t side = ctx->side;
@@ -173,7 +173,7 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         GenArgs ga;
         ga.A = A; ga.B = B; ga.lda = lda; ga.ldb = ldb;
         ga.n = n; ga.r = r; ga.j1 = j1; ga.qg = qg; ga.group = group;
-        ga.R = R[set]; ga.flags = fl;
+        ga.R = R[set]; ga.flags = fl; ga.qmax = L.qmax;
         ga.epoch = (unsigned long long)(group + 1) << 32;
         ga.status = ctx->d_status;
         ga.stall = (flags & HTS_FLAG_TEST_STALL) ? 1 : 0;

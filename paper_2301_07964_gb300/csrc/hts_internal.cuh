@@ -183,7 +183,8 @@ struct GenArgs {
     int lda, ldb;
     int n, r, j1, qg, group;
     ReflectorSet R;
-    unsigned long long *flags;   // one progress word per sweep slot
+    unsigned long long *flags;   // progress words: [0, qmax) main blocks, [qmax, 2 qmax) helpers
+    int qmax;
     unsigned long long epoch;    // (group + 1) << 32
     int *status;
     int stall;                   // fault injection: slot 0 never publishes (tests only)
