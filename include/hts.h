@@ -61,7 +61,8 @@ typedef enum {
  *             1 <= q <= r.  Default: r.
  *  p          stage-1 block height in units of r (Alg. 1); p >= 2 and p*r <= 128 (one
  *             block's RQ runs in shared memory).  Default: min(8, 128/r).
- *  emu_slices number of BF16 slices per FP64 operand in HTS_GEMM_EMU_BF16 mode.
+ *  emu_slices number of BF16 digits per FP64 operand in HTS_GEMM_EMU_BF16 mode: 0 or 8 (the
+ *             only value this build implements; others give HTS_ERR_UNSUPPORTED).
  *  tile_m, tile_n  reserved.
  *  flags      bit 0 (HTS_FLAG_NO_CLEAN): skip the final exact zeroing below the band.
  *             bit 30 (HTS_FLAG_TEST_STALL): fault injection for tests of the failure path:
@@ -91,7 +92,8 @@ void hts_destroy(hts_ctx *ctx);
 
 /* Bytes of `work` needed by hts_reduce_stage1 / hts_reduce_stage2 / hts_reduce for an n x n
  * pencil with r subdiagonals and parameters p (NULL = defaults).  The size covers all three
- * entry points. */
+ * entry points and both update modes (HTS_GEMM_EMU_BF16 adds 64 KiB per block of r columns
+ * for the digit planes of the reflector products). */
 hts_status hts_workspace_size(int n, int r, const hts_params *p, size_t *bytes);
 
 /*
@@ -115,6 +117,12 @@ hts_status hts_reduce_stage1(hts_ctx *ctx, int n, int r,
  * of A below the r-th subdiagonal and of B below the diagonal are treated as zero.  r = 1
  * (and n <= 2) is a no-op apart from HTS_COMP_INIT.  Reflectors act on rows/columns 2..n
  * only, so Q e_1 and Z e_1 are unchanged.
+ * mode selects the arithmetic of the delayed updates (Alg. 4): HTS_GEMM_FP64 applies the
+ * reflectors one at a time in native FP64; HTS_GEMM_EMU_BF16 forms each block's reflector
+ * product U_k (w x w, w = r + q - 1) and applies it as a product emulated on the BF16 tensor
+ * cores (8 base-256 digits per operand, FP32 accumulation of exact integer partial sums,
+ * result error below 2^-58 of each row window's largest entry); it requires r = 16
+ * (HTS_ERR_UNSUPPORTED otherwise).  The chase runs in native FP64 in both modes.
  */
 hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r,
                              double *A, int lda, double *B, int ldb,
@@ -149,7 +157,8 @@ hts_status hts_reduce_stage2_noalloc(hts_ctx *ctx, int n, int r,
 /*
  * Full reduction of a dense pencil: QR of B (stage 0; the paper QR-factorises B first,
  * Section "Experiments"), then stage 1 with n_b = r, then stage 2.  Requires 1 <= r < n and
- * r <= 32.  With HTS_COMP_INIT, Q e_1 = +-B(:,1)/||B(:,1)|| and Z e_1 = e_1.
+ * r <= 32.  With HTS_COMP_INIT, Q e_1 = +-B(:,1)/||B(:,1)|| and Z e_1 = e_1.  mode applies to
+ * stage 2's delayed updates (stages 0 and 1 run in native FP64).
  */
 hts_status hts_reduce(hts_ctx *ctx, int n, int r,
                       double *A, int lda, double *B, int ldb,

@@ -22,7 +22,11 @@ enum {
     HTS_K_STAGE1 = 4,       /* stage 0 / stage 1 kernels */
     HTS_K_APPLY_QZ = 5,     /* delayed right updates of Q and Z (stage 2, side stream) */
     HTS_K_BATCH = 6,        /* batched reduction of many small pencils */
-    HTS_K_NKINDS = 8
+    HTS_K_FORM_U = 7,       /* block formation: reflector products per block (stage 2) */
+    HTS_K_EMU_RIGHT = 8,    /* emulated-FP64 delayed right updates of A and B (stage 2) */
+    HTS_K_EMU_LEFT = 9,     /* emulated-FP64 delayed left updates of A and B (stage 2) */
+    HTS_K_EMU_QZ = 10,      /* emulated-FP64 delayed updates of Q and Z (stage 2, side stream) */
+    HTS_K_NKINDS = 12
 };
 
 typedef struct {
@@ -30,6 +34,7 @@ typedef struct {
     double ms;         /* summed CUDA-event durations of those launches */
     double flops;      /* algorithmic floating-point operations (4 per element and reflector) */
     double bytes;      /* algorithmic DRAM bytes (each touched element read and written once) */
+    double mma_flops;  /* BF16 tensor-core flops issued (emulated-FP64 kernels; 0 elsewhere) */
 } hts_kernel_profile;
 
 /* Start recording: preallocates 2 * max_launches CUDA events on the context's device (do

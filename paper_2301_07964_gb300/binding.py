@@ -38,14 +38,15 @@ class hts_params(ctypes.Structure):
                 ("tile_m", ctypes.c_int), ("tile_n", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
-HTS_K_NKINDS = 8
+HTS_K_NKINDS = 12
 KERNEL_KINDS = {0: "k_s2_generate", 1: "k_s2_apply_right", 2: "k_s2_apply_left", 3: "util", 4: "stage1",
-                5: "k_s2_apply_right_qz", 6: "k_reduce_batched"}
+                5: "k_s2_apply_right_qz", 6: "k_reduce_batched", 7: "k_s2_form_u", 8: "k_s2_emu_apply_right",
+                9: "k_s2_emu_apply_left", 10: "k_s2_emu_apply_qz"}
 
 
 class hts_kernel_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
-                ("bytes", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("mma_flops", ctypes.c_double)]
 
 
 class HTSError(RuntimeError):
@@ -236,7 +237,7 @@ def hts_profile_begin(ctx, max_launches: int):
 
 
 def hts_profile_end(ctx):
-    """Returns ({kind name: {launches, ms, flops, bytes}}, dropped)."""
+    """Returns ({kind name: {launches, ms, flops, bytes, mma_flops}}, dropped)."""
     out = (hts_kernel_profile * HTS_K_NKINDS)()
     dropped = ctypes.c_int(0)
     st = load().hts_profile_end(ctx, out, ctypes.byref(dropped))
@@ -246,7 +247,8 @@ def hts_profile_end(ctx):
     for k in range(HTS_K_NKINDS):
         if out[k].launches:
             res[KERNEL_KINDS.get(k, "kind%d" % k)] = dict(launches=out[k].launches, ms=out[k].ms,
-                                                         flops=out[k].flops, bytes=out[k].bytes)
+                                                         flops=out[k].flops, bytes=out[k].bytes,
+                                                         mma_flops=out[k].mma_flops)
     return res, dropped.value
 
 

@@ -1,0 +1,459 @@
+// Delayed updates of stage 2 as small dense products, in emulated FP64 on the BF16 tensor
+// cores (HTS_GEMM_EMU_BF16).
+//
+// Block formation (Alg. 4, "form compact WY" / the accumulated reflector blocks): for each
+// block k of a group, the group's qg reflectors of that block act on one window of
+// w = r + qg - 1 consecutive indices.  Their product in sweep order
+//     U^Z_k = Z^_k^{j1} Z^_k^{j1+1} ... Z^_k^{j1+qg-1},  U^Q_k = Q^_k^{j1} ... Q^_k^{j1+qg-1}
+// is formed explicitly as a w x w matrix (k_s2_form_u).  The delayed updates then become
+//     X(rows, window k) := X(rows, window k) U_k           (A, B rows above the band; Z; Q)
+//     X(window k, cols)^T := X(window k, cols)^T U^Q_k     (the left updates of A and B)
+// for k from the last block to the first; consecutive windows overlap in qg - 1 indices, so
+// a tile of rows keeps the overlap in registers and streams r new columns per block.
+//
+// Emulation.  Every operand is written as a fixed-point integer with a shared scale, x =
+// round(v 2^-unit), split into 8 balanced base-256 digits d_1..d_8 in [-128, 127]
+// (x = sum d_i 256^(8-i)); each digit is exact in BF16.  A product of a row window with U_k
+// is the sum over digit pairs (i, t) of (digits_i of the rows) (digits_t of U_k), weighted by
+// 256^-(i+t); pairs with the same level i + t share an FP32 accumulator, in which every partial
+// sum is an integer below 2^22 and hence exact.  Levels 2..9 are formed (36 products, each a
+// 16 x 8 x 16 BF16 mma.sync) and summed in 64-bit integer arithmetic; the dropped levels
+// weigh less than 2^-58 of the row's largest entry.  Row scales are powers of two taken from
+// the largest entry of each row window; U_k (orthogonal, entries in [-1, 1]) uses the fixed
+// scale 2^-61.  No FP64 instruction runs in the update loop: FP64 values enter and leave
+// through integer bit manipulation of their IEEE-754 encoding.
+#include "hts_internal.cuh"
+
+namespace hts {
+
+namespace {
+
+constexpr int kDigits = 8;                 // balanced base-256 digits per operand
+constexpr int kTopLevel = 9;               // digit pairs with i + t <= 9 are formed
+constexpr int kPlaneWords = kDigits * 2 * 4 * 32;   // uint2 words of one U_k (16 KiB)
+constexpr int kUnitU = -61;                // U_k entries as integers round(u 2^61)
+constexpr int kEmuWarps = 4;               // warps per apply block
+constexpr int kEmuRows = 16 * kEmuWarps;   // rows (or columns) per apply block
+constexpr int kZeroExp = -4000;            // "exponent" of a zero value
+
+// ---- IEEE-754 double <-> fixed point (integer arithmetic only) --------------------------
+
+// Smallest e with |v| < 2^e, or kZeroExp for zero and subnormal v (treated as zero).
+__device__ __forceinline__ int exp_of_f64(double v)
+{
+    const int eb = (int)((__double_as_longlong(v) >> 52) & 0x7ff);
+    return eb == 0 ? kZeroExp : eb - 1022;
+}
+
+// Smallest e with |x 2^unit| < 2^e, or kZeroExp.
+__device__ __forceinline__ int exp_of_fixed(long long x, int unit)
+{
+    if (x == 0) return kZeroExp;
+    const unsigned long long m = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+    return 64 - __clzll(m) + unit;
+}
+
+// round(v 2^-unit) for |v| < 2^(unit + 62); zero and subnormal v give 0.
+__device__ __forceinline__ long long f64_to_fixed(double v, int unit)
+{
+    const long long b = __double_as_longlong(v);
+    const int eb = (int)((b >> 52) & 0x7ff);
+    if (eb == 0) return 0;
+    const long long mant = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;   // v = +-mant 2^(eb-1075)
+    const int sh = eb - 1075 - unit;
+    long long x;
+    if (sh >= 0) x = mant << sh;
+    else if (sh > -63) x = (mant + (1LL << (-sh - 1))) >> (-sh);
+    else x = 0;
+    return b < 0 ? -x : x;
+}
+
+// x 2^unit rounded to the nearest double (ties to even); results below the normal range
+// become signed zero.
+__device__ __forceinline__ double fixed_to_f64(long long x, int unit)
+{
+    if (x == 0) return 0.0;
+    const unsigned long long sgn = x < 0 ? 0x8000000000000000ULL : 0ULL;
+    unsigned long long m = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+    const int lz = __clzll(m);
+    m <<= lz;                                    // leading one at bit 63
+    const int eb = 63 - lz + unit + 1023;        // biased exponent of the result
+    if (eb <= 0) return __longlong_as_double((long long)sgn);
+    unsigned long long mant = m >> 11;           // 53 bits including the leading one
+    const unsigned long long rem = m & 0x7ffULL;
+    if (rem > 0x400ULL || (rem == 0x400ULL && (mant & 1ULL))) ++mant;
+    // the leading one of mant adds 1 to the exponent field; a rounding carry adds one more
+    const unsigned long long bits = ((unsigned long long)(eb - 1) << 52) + mant;
+    return __longlong_as_double((long long)(sgn | bits));
+}
+
+// x 2^su expressed in units 2^du (rounded), for values known to fit.
+__device__ __forceinline__ long long refix(long long x, int su, int du)
+{
+    const int s = su - du;
+    if (s >= 0) return x << s;
+    if (s > -63) return (x + (1LL << (-s - 1))) >> (-s);
+    return 0;
+}
+
+// ---- balanced digits --------------------------------------------------------------------
+
+// BF16 bit patterns of the 8 balanced base-256 digits of x (|x| < 2^62), most significant
+// first: with u = x + 0x8080808080808080 (no wrap-around in that range), digit i is byte
+// (8 - i) of u minus 128.  A digit in [-128, 127] is formed exactly in FP32 from its byte and
+// its FP32 encoding has 16 trailing zero bits, so the upper half is the exact BF16.
+__device__ __forceinline__ void digits_bf16(long long x, unsigned (&bf)[kDigits])
+{
+    const unsigned long long u = (unsigned long long)x + 0x8080808080808080ULL;
+    const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+#pragma unroll
+    for (int i = 0; i < kDigits; ++i) {
+        const unsigned word = (i < 4) ? hi : lo;
+        const unsigned byte = (word >> (8 * (3 - (i & 3)))) & 0xffu;
+        const float f = __uint_as_float(0x4B000000u | byte) - 8388736.0f;   // byte - 128
+        bf[i] = __float_as_uint(f) >> 16;
+    }
+}
+
+__device__ __forceinline__ unsigned pack_bf16(unsigned lo, unsigned hi) { return lo | (hi << 16); }
+
+// An FP32 value holding an integer of magnitude below 2^22, as int (exact).
+__device__ __forceinline__ int f32_exact_int(float c) { return __float_as_int(c + 12582912.0f) - 0x4B400000; }
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Block formation: one warp per (block k, reflector family).  U (w x w, zero padded to
+// 32 x 32) starts as the identity and is multiplied from the right by the group's reflectors
+// of block k in sweep order (lane = row of U).  The result is stored as digit planes laid
+// out as the B operand of mma.m16n8k16: word ((t * 2 + kt) * 4 + nt) * 32 + lane holds, for
+// lane = 4 g + c, the digit t of U(16 kt + 2c + {0, 1}, 8 nt + g) and of
+// U(16 kt + 2c + {8, 9}, 8 nt + g).
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_s2_form_u(FormUArgs a)
+{
+    __shared__ double Us[4][32 * 33];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.x * 4 + warp;
+    const int fam = blockIdx.y;   // 0: Q^ reflectors, 1: Z^ reflectors
+    const int kmax = nblocks_gen(a.n, a.r, a.j1) - 1;
+    if (k > kmax || __ldcg(a.status) != 0) return;   // no block-wide barrier follows
+    const int w = a.r + a.qg - 1;
+    const int kdim = a.R.kdim;
+    double *U = Us[warp];
+    for (int c = 0; c < 32; ++c) U[lane * 33 + c] = (lane == c && lane < w) ? 1.0 : 0.0;
+    const double *V = fam ? a.R.VZ : a.R.VQ;
+    const double *T = fam ? a.R.TZ : a.R.TQ;
+    for (int s = 0; s < a.qg; ++s) {
+        const double tau = __ldcg(T + (size_t)s * kdim + k);
+        if (tau == 0.0) continue;
+        const int mlen = imin(a.r, a.n - (a.j1 + s + k * a.r));
+        const double *v = V + ((size_t)s * kdim + k) * a.r;
+        double *row = U + lane * 33 + s;
+        double d0 = 0.0, d1 = 0.0;
+        for (int i = 0; i < mlen; i += 2) {
+            d0 = fma(row[i], __ldcg(v + i), d0);
+            if (i + 1 < mlen) d1 = fma(row[i + 1], __ldcg(v + i + 1), d1);
+        }
+        const double d = (d0 + d1) * tau;
+        for (int i = 0; i < mlen; ++i) row[i] = fma(-d, __ldcg(v + i), row[i]);
+    }
+    __syncwarp();
+    const int g = lane >> 2, c = lane & 3;
+    uint2 *out = (fam ? a.planesZ : a.planesQ) + (size_t)k * kPlaneWords;
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int col = 8 * nt + g, r0 = 16 * kt + 2 * c;
+            unsigned e0[kDigits], e1[kDigits], e8[kDigits], e9[kDigits];
+            digits_bf16(f64_to_fixed(U[r0 * 33 + col], kUnitU), e0);
+            digits_bf16(f64_to_fixed(U[(r0 + 1) * 33 + col], kUnitU), e1);
+            digits_bf16(f64_to_fixed(U[(r0 + 8) * 33 + col], kUnitU), e8);
+            digits_bf16(f64_to_fixed(U[(r0 + 9) * 33 + col], kUnitU), e9);
+#pragma unroll
+            for (int t = 0; t < kDigits; ++t)
+                out[((t * 2 + kt) * 4 + nt) * 32 + lane] = make_uint2(pack_bf16(e0[t], e1[t]), pack_bf16(e8[t], e9[t]));
+        }
+}
+
+// ---------------------------------------------------------------------------------------
+// Emulated delayed update.  Each warp owns 16 lines (rows of X for the right updates,
+// columns of X for the left updates) and a window of 32 positions (window index p = column
+// c0 + p, or row R0 + p, with c0 = R0 = j1 + k r + 1).  Lane 4 g + c holds lines g and g + 8
+// at positions 16 kt + 8 h + 2 c + {0, 1} (kt, h in {0, 1}): exactly the A-operand positions
+// of mma.m16n8k16 and the result positions of its accumulator, so a window's result feeds
+// the next window without data movement (positions p < w - r move to p + r, i.e. kt 0 -> 1;
+// this needs r = 16).
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kEmuWarps * 32) k_s2_emu_apply(EmuArgs a)
+{
+    __shared__ __align__(16) uint2 planes[2][kPlaneWords];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, c = lane & 3;
+    const int n = a.n, r = a.r, j1 = a.j1, qg = a.qg;
+    const int w = r + qg - 1;
+    const int mi = blockIdx.y;
+    const int kind = a.kind[mi];
+    const bool left = kind >= 4;
+    double *X = a.M[mi];
+    const size_t ld = (size_t)a.ld[mi];
+    const uint2 *P = (kind == 3 || left) ? a.planesQ : a.planesZ;
+    const int kmax = nblocks_gen(n, r, j1) - 1;
+    const int jl = j1 + qg - 1;
+    if (__ldcg(a.status) != 0) return;
+
+    // lines of this block; left updates walk the column tiles from the right
+    const int tile = left ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    const int l0 = tile * kEmuRows + 1;
+    const int llast = imin(l0 + kEmuRows - 1, n);
+    int kbeg = kmax, kend = 0;
+    if (kind <= 1) {
+        // rows of A and B: blocks whose whole reflector set is still pending for every row
+        // of the tile (the rest, the staircase, is left to the FP64 kernel)
+        const int kT = (llast <= j1) ? -1 : qg + (llast - j1 - 1) / r;
+        kend = kT + 1;
+    } else if (left) {
+        const int isB = kind == 5;
+        kbeg = -1;
+        for (int k = kmax; k >= 0; --k) {
+            const int cut = isB ? imin(jl + (k + 1) * r, n) : jl + imax(0, (k - 1) * r + 1);
+            if (cut < llast) { kbeg = k; break; }
+        }
+    }
+    if (kbeg < kend || l0 > n) return;
+
+    const int lineA = l0 + warp * 16 + g, lineB = lineA + 8;   // lines of rr = 0, 1
+    auto addr = [=](int ln, int p, int k) -> double * {
+        const int pos = j1 + k * r + 1 + p;   // matrix column (right) or row (left)
+        return left ? X + (size_t)(pos - 1) + (size_t)(ln - 1) * ld : X + (size_t)(ln - 1) + (size_t)(pos - 1) * ld;
+    };
+    auto valid = [=](int ln, int p, int k) -> bool { return ln <= n && p < w && j1 + k * r + 1 + p <= n; };
+
+    // U planes of block kbeg
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(P + (size_t)kbeg * kPlaneWords);
+        uint4 *dst = reinterpret_cast<uint4 *>(planes[0]);
+        for (int e = tid; e < kPlaneWords / 2; e += kEmuWarps * 32) cp_async16(dst + e, src + e);
+        cp_async_commit();
+    }
+
+    long long xv[2][2][2][2];   // [line][kt][h][pair] window values, xv 2^unit[line]
+    double dv[2][2][2];         // [line][h][pair] FP64 values entering at kt = 0
+    int unit[2];
+    // first window: positions of kt = 1 in fixed point at their own scale, kt = 0 as FP64
+    {
+        int em[2] = {kZeroExp, kZeroExp};
+        double v1[2][2][2];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                    const int ln = rr ? lineB : lineA;
+                    const int p = 8 * h + 2 * c + pr;
+                    dv[rr][h][pr] = valid(ln, p, kbeg) ? *addr(ln, p, kbeg) : 0.0;
+                    v1[rr][h][pr] = valid(ln, p + 16, kbeg) ? *addr(ln, p + 16, kbeg) : 0.0;
+                    em[rr] = imax(em[rr], exp_of_f64(v1[rr][h][pr]));
+                }
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            em[rr] = imax(em[rr], __shfl_xor_sync(0xffffffffu, em[rr], 1));
+            em[rr] = imax(em[rr], __shfl_xor_sync(0xffffffffu, em[rr], 2));
+            unit[rr] = (em[rr] == kZeroExp ? 0 : em[rr] + 2) - 64;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                    xv[rr][1][h][pr] = f64_to_fixed(v1[rr][h][pr], unit[rr]);
+                    xv[rr][0][h][pr] = 0;
+                }
+        }
+    }
+
+    for (int k = kbeg; k >= kend; --k) {
+        const bool last = (k == kend);
+        const int buf = (kbeg - k) & 1;
+        // next block's planes
+        if (!last) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(P + (size_t)(k - 1) * kPlaneWords);
+            uint4 *dst = reinterpret_cast<uint4 *>(planes[buf ^ 1]);
+            for (int e = tid; e < kPlaneWords / 2; e += kEmuWarps * 32) cp_async16(dst + e, src + e);
+        }
+        cp_async_commit();
+
+        // ---- scale of each line: the largest entry of its window
+        int ua[2];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            int em = kZeroExp;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                    em = imax(em, exp_of_f64(dv[rr][h][pr]));
+                    em = imax(em, exp_of_fixed(xv[rr][1][h][pr], unit[rr]));
+                }
+            em = imax(em, __shfl_xor_sync(0xffffffffu, em, 1));
+            em = imax(em, __shfl_xor_sync(0xffffffffu, em, 2));
+            ua[rr] = (em == kZeroExp ? 0 : em + 2) - 64;   // |x| < 2^62
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                    xv[rr][0][h][pr] = f64_to_fixed(dv[rr][h][pr], ua[rr]);
+                    xv[rr][1][h][pr] = refix(xv[rr][1][h][pr], unit[rr], ua[rr]);
+                }
+        }
+
+        // ---- new columns of the next window (positions 0 .. r-1)
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                    const int ln = rr ? lineB : lineA;
+                    const int p = 8 * h + 2 * c + pr;
+                    dv[rr][h][pr] = (!last && valid(ln, p, k - 1)) ? *addr(ln, p, k - 1) : 0.0;
+                }
+
+        // ---- A operands: digits of the window
+        unsigned af[kDigits][2][4];
+#pragma unroll
+        for (int kt = 0; kt < 2; ++kt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr) {
+                    unsigned d0[kDigits], d1[kDigits];
+                    digits_bf16(xv[rr][kt][h][0], d0);
+                    digits_bf16(xv[rr][kt][h][1], d1);
+#pragma unroll
+                    for (int t = 0; t < kDigits; ++t) af[t][kt][2 * h + rr] = pack_bf16(d0[t], d1[t]);
+                }
+
+        // ---- line activity (left updates: columns right of the cut of block k)
+        bool act0 = true, act1 = true;
+        if (left) {
+            const int cut = (kind == 5) ? imin(jl + (k + 1) * r, n) : jl + imax(0, (k - 1) * r + 1);
+            act0 = lineA > cut;
+            act1 = lineB > cut;
+        }
+
+        cp_async_wait<1>();
+        __syncthreads();
+        const uint2 *pl = planes[buf];
+
+        // ---- products, one n-tile (8 output positions) at a time; results replace xv
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            float acc[kTopLevel - 1][4];
+#pragma unroll
+            for (int d = 0; d < kTopLevel - 1; ++d)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[d][e] = 0.0f;
+#pragma unroll
+            for (int t = 0; t < kDigits; ++t) {
+                const uint2 b0 = pl[((t * 2 + 0) * 4 + nt) * 32 + lane];
+                const uint2 b1 = pl[((t * 2 + 1) * 4 + nt) * 32 + lane];
+#pragma unroll
+                for (int i = 0; i < kDigits; ++i) {
+                    if (i + t + 2 <= kTopLevel) {   // level (i+1) + (t+1)
+                        mma_bf16(acc[i + t], af[i][0], b0.x, b0.y);
+                        mma_bf16(acc[i + t], af[i][1], b1.x, b1.y);
+                    }
+                }
+            }
+            // levels 2..9 -> one integer in units 2^(ua + 3): level L weighs 2^(8 (8 - L))
+            const int kt = nt >> 1, h = nt & 1;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c2 = f32_exact_int(acc[0][e]), c3 = f32_exact_int(acc[1][e]);
+                const int c4 = f32_exact_int(acc[2][e]), c5 = f32_exact_int(acc[3][e]);
+                const int c6 = f32_exact_int(acc[4][e]), c7 = f32_exact_int(acc[5][e]);
+                const int c8 = f32_exact_int(acc[6][e]), c9 = f32_exact_int(acc[7][e]);
+                const int lo = (c7 << 8) + c8 + ((c9 + 128) >> 8);
+                const int mid = (c5 << 8) + c6;
+                const long long hi = ((long long)c2 << 16) + (long long)((c3 << 8) + c4);
+                const long long val = (hi << 32) + ((long long)mid << 16) + (long long)lo;
+                const int rr = e >> 1, pr = e & 1;
+                const bool act = rr ? act1 : act0;
+                xv[rr][kt][h][pr] = act ? val : refix(xv[rr][kt][h][pr], ua[rr], ua[rr] + 3);
+            }
+        }
+        __syncthreads();   // planes[buf] is refilled by the next iteration's copy
+
+        // ---- finished positions leave the window (all positions after the last block)
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int ln = rr ? lineB : lineA;
+            unit[rr] = ua[rr] + 3;
+#pragma unroll
+            for (int kt = 0; kt < 2; ++kt)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int pr = 0; pr < 2; ++pr) {
+                        const int p = 16 * kt + 8 * h + 2 * c + pr;
+                        if ((last || p >= w - r) && valid(ln, p, k))
+                            *addr(ln, p, k) = fixed_to_f64(xv[rr][kt][h][pr], unit[rr]);
+                    }
+            // slide: positions p < w - r move to p + r (kt 0 -> 1)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                    const int p = 8 * h + 2 * c + pr;
+                    xv[rr][1][h][pr] = (p < w - r) ? xv[rr][0][h][pr] : 0;
+                }
+        }
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------
+size_t emu_plane_bytes(int kdim) { return (size_t)kdim * kPlaneWords * sizeof(uint2); }
+
+bool emu_supported(int r, int qg) { return r == 16 && qg >= 1 && r + qg - 1 <= 32; }
+
+int emu_tile_rows() { return kEmuRows; }
+
+cudaError_t launch_s2_form_u(const FormUArgs &a, cudaStream_t st)
+{
+    const int kmax = nblocks_gen(a.n, a.r, a.j1) - 1;
+    if (kmax < 0) return cudaSuccess;
+    dim3 grid((kmax + 1 + 3) / 4, 2);
+    k_s2_form_u<<<grid, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_s2_emu_apply(const EmuArgs &a, int nmat, cudaStream_t st)
+{
+    if (nmat <= 0) return cudaSuccess;
+    dim3 grid((a.n + kEmuRows - 1) / kEmuRows, nmat);
+    k_s2_emu_apply<<<grid, kEmuWarps * 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace hts

@@ -27,11 +27,13 @@ struct DeviceGuard {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Workspace layout of stage 2: two reflector sets (group g uses set g mod 2, so the Q / Z
-// update of group g can still read its set while group g+1 generates into the other one) and
-// one progress word per sweep slot.
+// update of group g can still read its set while group g+1 generates into the other one), one
+// progress word per sweep slot and, for the emulated updates, the digit planes of the
+// blocks' reflector products (one plane set per reflector set).
 struct S2Layout {
     int kdim, qmax;
-    size_t off_vq[2], off_tq[2], off_vz[2], off_tz[2], off_flags, total;
+    size_t off_vq[2], off_tq[2], off_vz[2], off_tz[2], off_flags, total_fp64;
+    size_t off_pq[2], off_pz[2], total;
 };
 
 S2Layout s2_layout(int n, int r)
@@ -49,8 +51,20 @@ S2Layout s2_layout(int n, int r)
         L.off_tz[b] = o; o = align_up(o + nt, 256);
     }
     L.off_flags = o; o = align_up(o + 2 * (size_t)L.qmax * sizeof(unsigned long long), 256);
+    L.total_fp64 = o;
+    const size_t np = emu_plane_bytes(L.kdim);
+    for (int b = 0; b < 2; ++b) {
+        L.off_pq[b] = o; o = align_up(o + np, 256);
+        L.off_pz[b] = o; o = align_up(o + np, 256);
+    }
     L.total = o;
     return L;
+}
+
+size_t s2_bytes(int n, int r, hts_gemm_mode mode)
+{
+    const S2Layout L = s2_layout(n, r);
+    return mode == HTS_GEMM_EMU_BF16 ? L.total : L.total_fp64;
 }
 
 bool bad_matrix(const double *M, int ld, int n) { return M == nullptr || ld < (n > 1 ? n : 1); }
@@ -72,6 +86,15 @@ hts_status check_common(hts_ctx *ctx, int n, int r, const double *A, int lda, co
 
 hts_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HTS_OK : HTS_ERR_CUDA; }
 
+// The emulated updates keep one window of r + q - 1 <= 32 indices in the registers of a warp
+// and slide it by one 16-wide operand tile per block: r = 16 only, with 8 digits per operand.
+hts_status check_emu(hts_gemm_mode mode, int r, int q, const hts_params *p)
+{
+    if (mode != HTS_GEMM_EMU_BF16) return HTS_OK;
+    if (p && p->emu_slices != 0 && p->emu_slices != 8) return HTS_ERR_UNSUPPORTED;
+    return emu_supported(r, q) ? HTS_OK : HTS_ERR_UNSUPPORTED;
+}
+
 // Block height (in units of r) of stage 1: the paper's p = 8 by default, limited so that one
 // p*r x p*r B block fits in shared memory for its RQ (p*r <= 128).
 int stage1_p(const hts_params *prm, int r)
@@ -86,13 +109,23 @@ int stage1_p(const hts_params *prm, int r)
 // and written once (16 bytes).
 struct GroupCost {
     double f_gen, b_gen, f_right, b_right, f_qz, b_qz, f_left, b_left;
+    double f_stair, b_stair, m_right, m_qz, m_left, f_form;   // emulated mode
 };
 
-GroupCost s2_group_cost(int n, int r, int j1, int qg, bool hasQ, bool hasZ)
+// First block of row tile T (of `rows` rows) that the emulated right update of A and B does
+// not take: blocks k > kT(T) have their whole reflector set pending for every row of T.
+int emu_tile_kT(int n, int r, int j1, int qg, int rows, int x)
+{
+    const int xt = imin(((x - 1) / rows + 1) * rows, n);
+    return (xt <= j1) ? -1 : qg + (xt - j1 - 1) / r;
+}
+
+GroupCost s2_group_cost(int n, int r, int j1, int qg, bool hasQ, bool hasZ, bool emu)
 {
     GroupCost c{};
     const int jl = j1 + qg - 1;
     const int kmax = nblocks_gen(n, r, j1) - 1;
+    const int er = emu_tile_rows();
     for (int j = j1; j <= jl; ++j) {
         const int kg = nblocks_gen(n, r, j);
         for (int k = 0; k < kg; ++k) {
@@ -104,20 +137,35 @@ GroupCost s2_group_cost(int n, int r, int j1, int qg, bool hasQ, bool hasZ)
             c.f_gen += 8.0 * m * (j - j1) + 4.0 * m * m + rq + 4.0 * m * (rowsA + rowsB);
             c.b_gen += 16.0 * (m * (rowsA + rowsB) + m * m + 2.0 * (m + j - j1));
             const double above = g.i4 - 1;   // rows of A and B the apply phase updates
-            c.f_right += 4.0 * m * 2.0 * above;
+            double stair = 0.0;
+            if (emu) {
+                // rows x < i4 of tiles with kT >= k stay with the FP64 staircase kernel
+                for (int x = 1; x <= (int)above; x += er)
+                    if (emu_tile_kT(n, r, j1, qg, er, x) >= k) stair += imin(er, (int)above - x + 1);
+            }
+            c.f_right += 4.0 * m * 2.0 * (above - stair);
+            c.f_stair += 4.0 * m * 2.0 * stair;
             c.f_qz += 4.0 * m * ((hasZ ? n : 0) + (hasQ ? n : 0));
             const int cutA = jl + imax(0, (k - 1) * r + 1);
             const int cutB = imin(jl + (k + 1) * r, n);
             c.f_left += 4.0 * m * ((double)imax(0, n - cutA) + imax(0, n - cutB));
+            c.f_form += 2.0 * 4.0 * m * (r + qg - 1);
         }
     }
     // right: rows x of A and B from the first block they need to column n; Z, Q all of it
-    double elems = 0.0;
+    double elems = 0.0, stair_elems = 0.0;
     for (int x = 1; x <= n; ++x) {
         const int kf = (x <= j1) ? 0 : (x - j1 - 1) / r + 2;
-        if (kf <= kmax) elems += n - (j1 + kf * r);
+        if (kf <= kmax) {
+            elems += n - (j1 + kf * r);
+            if (emu) {
+                const int kT = imin(kmax, emu_tile_kT(n, r, j1, qg, er, x));
+                if (kT >= kf) stair_elems += imin(n, j1 + kT * r + r + qg - 1) - (j1 + kf * r);
+            }
+        }
     }
-    c.b_right = 16.0 * 2.0 * elems;
+    c.b_right = 16.0 * 2.0 * (elems - stair_elems);
+    c.b_stair = 16.0 * 2.0 * stair_elems;
     c.b_qz = 16.0 * ((hasZ ? 1 : 0) + (hasQ ? 1 : 0)) * (double)n * (n - j1);
     // left: column c of A / B from row j1+1 down to the bottom of the lowest block it needs
     double le = 0.0;
@@ -131,24 +179,45 @@ GroupCost s2_group_cost(int n, int r, int j1, int qg, bool hasQ, bool hasZ)
             le += (double)ncol * rows;
         }
     c.b_left = 16.0 * le;
+    if (emu) {
+        // tensor-core work: 288 mma.m16n8k16 (4096 flops each) per warp and window step
+        const double step = 4.0 * 288.0 * 4096.0;   // one 64-line tile (4 warps)
+        const int ntile = (n + er - 1) / er;
+        for (int t = 0; t < ntile; ++t) {
+            const int l0 = t * er + 1, llast = imin(l0 + er - 1, n);
+            const int kT = (llast <= j1) ? -1 : qg + (llast - j1 - 1) / r;
+            if (kmax > kT) c.m_right += 2.0 * step * (kmax - kT);
+            c.m_qz += step * (kmax + 1) * ((hasZ ? 1 : 0) + (hasQ ? 1 : 0));
+            for (int isB = 0; isB < 2; ++isB)
+                for (int k = kmax; k >= 0; --k) {
+                    const int cut = isB ? imin(jl + (k + 1) * r, n) : jl + imax(0, (k - 1) * r + 1);
+                    if (cut < llast) { c.m_left += step * (k + 1); break; }
+                }
+        }
+    }
     return c;
 }
 
 }  // namespace
 
-// Bytes of caller scratch stage 2 alone needs (two reflector sets and the progress words).
-size_t stage2_workspace_bytes(int n, int r) { return s2_layout(n, r).total; }
+// Bytes of caller scratch stage 2 alone needs in native FP64 mode (two reflector sets and
+// the progress words).
+size_t stage2_workspace_bytes(int n, int r) { return s2_layout(n, r).total_fp64; }
 
 // Stage 2 driver: the group loop of generate / apply launches.
 hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B, int ldb,
-                      double *Q, int ldq, double *Z, int ldz, int q, int flags,
+                      double *Q, int ldq, double *Z, int ldz, int q, int flags, hts_gemm_mode mode,
                       void *work, cudaStream_t st)
 {
     if (n <= 2 || r <= 1) return HTS_OK;
     const S2Layout L = s2_layout(n, r);
     char *w = static_cast<char *>(work);
+    const bool emu = mode == HTS_GEMM_EMU_BF16;
     ReflectorSet R[2];
+    uint2 *PQ[2], *PZ[2];
     for (int b = 0; b < 2; ++b) {
+        PQ[b] = reinterpret_cast<uint2 *>(w + L.off_pq[b]);
+        PZ[b] = reinterpret_cast<uint2 *>(w + L.off_pz[b]);
         R[b].VQ = reinterpret_cast<double *>(w + L.off_vq[b]);
         R[b].TQ = reinterpret_cast<double *>(w + L.off_tq[b]);
         R[b].VZ = reinterpret_cast<double *>(w + L.off_vz[b]);
@@ -165,7 +234,7 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
     for (int j1 = 1; j1 <= n - 2; j1 += q, ++group) {
         const int qg = imin(q, n - 2 - j1 + 1);
         const int set = group & 1;
-        const GroupCost gc = ctx->prof.enabled ? s2_group_cost(n, r, j1, qg, Q != nullptr, Z != nullptr)
+        const GroupCost gc = ctx->prof.enabled ? s2_group_cost(n, r, j1, qg, Q != nullptr, Z != nullptr, emu)
                                                : GroupCost{};
         // the Q / Z update of group-2 must be done with this reflector set
         if (qz && group >= 2 && cudaStreamWaitEvent(st, ctx->ev_qz[set], 0) != cudaSuccess) return HTS_ERR_CUDA;
@@ -183,21 +252,56 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
             ps.done(HTS_K_GENERATE, gc.f_gen, gc.b_gen);
         }
 
+        if (emu) {
+            // block formation, then the delayed updates as emulated products
+            FormUArgs fa;
+            fa.n = n; fa.r = r; fa.j1 = j1; fa.qg = qg; fa.R = R[set];
+            fa.planesQ = PQ[set]; fa.planesZ = PZ[set]; fa.status = ctx->d_status;
+            {
+                ProfScope ps(ctx, st);
+                if ((e = launch_s2_form_u(fa, st)) != cudaSuccess) return HTS_ERR_CUDA;
+                ps.done(HTS_K_FORM_U, gc.f_form, 0.0);
+            }
+            EmuArgs ea;
+            ea.M[0] = A; ea.ld[0] = lda; ea.kind[0] = 0;
+            ea.M[1] = B; ea.ld[1] = ldb; ea.kind[1] = 1;
+            for (int i = 2; i < 4; ++i) { ea.M[i] = nullptr; ea.ld[i] = 1; ea.kind[i] = 0; }
+            ea.n = n; ea.r = r; ea.j1 = j1; ea.qg = qg;
+            ea.planesQ = PQ[set]; ea.planesZ = PZ[set]; ea.status = ctx->d_status;
+            {
+                ProfScope ps(ctx, st);
+                if ((e = launch_s2_emu_apply(ea, 2, st)) != cudaSuccess) return HTS_ERR_CUDA;
+                ps.done(HTS_K_EMU_RIGHT, gc.f_right, gc.b_right, gc.m_right);
+            }
+        }
+
         ApplyArgs aa;
         aa.M[0] = A; aa.ld[0] = lda; aa.kind[0] = 0;
         aa.M[1] = B; aa.ld[1] = ldb; aa.kind[1] = 1;
         for (int i = 2; i < 4; ++i) { aa.M[i] = nullptr; aa.ld[i] = 1; aa.kind[i] = 0; }
         aa.n = n; aa.r = r; aa.j1 = j1; aa.qg = qg; aa.R = R[set]; aa.status = ctx->d_status;
+        aa.emu_rows = emu ? emu_tile_rows() : 0;
         {
             ProfScope ps(ctx, st);
             if ((e = launch_s2_apply_right(aa, 2, st)) != cudaSuccess) return HTS_ERR_CUDA;
-            ps.done(HTS_K_APPLY_RIGHT, gc.f_right, gc.b_right);
+            if (emu) ps.done(HTS_K_APPLY_RIGHT, gc.f_stair, gc.b_stair);
+            else ps.done(HTS_K_APPLY_RIGHT, gc.f_right, gc.b_right);
         }
 
-        LeftArgs la;
-        la.A = A; la.B = B; la.lda = lda; la.ldb = ldb;
-        la.n = n; la.r = r; la.j1 = j1; la.qg = qg; la.R = R[set]; la.status = ctx->d_status;
-        {
+        if (emu) {
+            EmuArgs el;
+            el.M[0] = A; el.ld[0] = lda; el.kind[0] = 4;
+            el.M[1] = B; el.ld[1] = ldb; el.kind[1] = 5;
+            for (int i = 2; i < 4; ++i) { el.M[i] = nullptr; el.ld[i] = 1; el.kind[i] = 0; }
+            el.n = n; el.r = r; el.j1 = j1; el.qg = qg;
+            el.planesQ = PQ[set]; el.planesZ = PZ[set]; el.status = ctx->d_status;
+            ProfScope ps(ctx, st);
+            if ((e = launch_s2_emu_apply(el, 2, st)) != cudaSuccess) return HTS_ERR_CUDA;
+            ps.done(HTS_K_EMU_LEFT, gc.f_left, gc.b_left, gc.m_left);
+        } else {
+            LeftArgs la;
+            la.A = A; la.B = B; la.lda = lda; la.ldb = ldb;
+            la.n = n; la.r = r; la.j1 = j1; la.qg = qg; la.R = R[set]; la.status = ctx->d_status;
             ProfScope ps(ctx, st);
             if ((e = launch_s2_apply_left(la, st)) != cudaSuccess) return HTS_ERR_CUDA;
             ps.done(HTS_K_APPLY_LEFT, gc.f_left, gc.b_left);
@@ -207,13 +311,25 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         if (qz) {
             if (cudaEventRecord(ctx->ev_gen[set], st) != cudaSuccess) return HTS_ERR_CUDA;
             if (cudaStreamWaitEvent(side, ctx->ev_gen[set], 0) != cudaSuccess) return HTS_ERR_CUDA;
-            ApplyArgs aq;
-            int nq = 0;
-            if (Z) { aq.M[nq] = Z; aq.ld[nq] = ldz; aq.kind[nq] = 2; ++nq; }
-            if (Q) { aq.M[nq] = Q; aq.ld[nq] = ldq; aq.kind[nq] = 3; ++nq; }
-            for (int i = nq; i < 4; ++i) { aq.M[i] = nullptr; aq.ld[i] = 1; aq.kind[i] = 0; }
-            aq.n = n; aq.r = r; aq.j1 = j1; aq.qg = qg; aq.R = R[set]; aq.status = ctx->d_status;
-            {
+            if (emu) {
+                EmuArgs eq;
+                int nq = 0;
+                if (Z) { eq.M[nq] = Z; eq.ld[nq] = ldz; eq.kind[nq] = 2; ++nq; }
+                if (Q) { eq.M[nq] = Q; eq.ld[nq] = ldq; eq.kind[nq] = 3; ++nq; }
+                for (int i = nq; i < 4; ++i) { eq.M[i] = nullptr; eq.ld[i] = 1; eq.kind[i] = 0; }
+                eq.n = n; eq.r = r; eq.j1 = j1; eq.qg = qg;
+                eq.planesQ = PQ[set]; eq.planesZ = PZ[set]; eq.status = ctx->d_status;
+                ProfScope ps(ctx, side);
+                if ((e = launch_s2_emu_apply(eq, nq, side)) != cudaSuccess) return HTS_ERR_CUDA;
+                ps.done(HTS_K_EMU_QZ, gc.f_qz, gc.b_qz, gc.m_qz);
+            } else {
+                ApplyArgs aq;
+                int nq = 0;
+                if (Z) { aq.M[nq] = Z; aq.ld[nq] = ldz; aq.kind[nq] = 2; ++nq; }
+                if (Q) { aq.M[nq] = Q; aq.ld[nq] = ldq; aq.kind[nq] = 3; ++nq; }
+                for (int i = nq; i < 4; ++i) { aq.M[i] = nullptr; aq.ld[i] = 1; aq.kind[i] = 0; }
+                aq.n = n; aq.r = r; aq.j1 = j1; aq.qg = qg; aq.R = R[set]; aq.status = ctx->d_status;
+                aq.emu_rows = 0;
                 ProfScope ps(ctx, side);
                 if ((e = launch_s2_apply_right(aq, nq, side)) != cudaSuccess) return HTS_ERR_CUDA;
                 ps.done(HTS_K_APPLY_QZ, gc.f_qz, gc.b_qz);
@@ -304,7 +420,7 @@ void hts_destroy(hts_ctx *ctx)
 hts_status hts_workspace_size(int n, int r, const hts_params *p, size_t *bytes)
 {
     if (!bytes || n < 0 || r < 1) return HTS_ERR_ARG;
-    const size_t s2 = s2_layout(n, r).total;
+    const size_t s2 = s2_layout(n, r).total;   // covers both update modes
     const size_t s01 = stage01_workspace_bytes(n, r, stage1_p(p, r));
     *bytes = s2 > s01 ? s2 : s01;
     return HTS_OK;
@@ -318,14 +434,14 @@ hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, dou
     hts_status s = check_common(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode);
     if (s != HTS_OK || n == 0) return s;
     if (r > kMaxR) return HTS_ERR_UNSUPPORTED;
-    if (mode != HTS_GEMM_FP64) return HTS_ERR_UNSUPPORTED;
     int q = (p && p->q > 0) ? p->q : r;
     if (q > r) return HTS_ERR_ARG;
+    if ((s = check_emu(mode, r, q, p)) != HTS_OK) return s;
     const int flags = p ? p->flags : 0;
     const bool needs_work = n > 2 && r > 1;
     if (needs_work) {
         if (!work || (reinterpret_cast<uintptr_t>(work) & 255u)) return HTS_ERR_WORKSPACE;
-        if (work_bytes < s2_layout(n, r).total) return HTS_ERR_WORKSPACE;
+        if (work_bytes < s2_bytes(n, r, mode)) return HTS_ERR_WORKSPACE;
     }
     DeviceGuard g(ctx->device);
     if (!g.ok) return HTS_ERR_CUDA;
@@ -338,7 +454,7 @@ hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, dou
         if (compz == HTS_COMP_INIT && (s = cuda_status(launch_set_identity(Z, ldz, n, st))) != HTS_OK) return s;
         ps.done(HTS_K_UTIL, 0.0, 0.0);
     }
-    return run_stage2(ctx, n, r, A, lda, B, ldb, Qp, ldq, Zp, ldz, q, flags, work, st);
+    return run_stage2(ctx, n, r, A, lda, B, ldb, Qp, ldq, Zp, ldz, q, flags, mode, work, st);
 }
 
 static hts_status check_stage1_args(hts_ctx *ctx, int n, int r, const hts_params *p, void *work, size_t work_bytes)
@@ -385,7 +501,6 @@ hts_status hts_reduce(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
 {
     hts_status s = check_common(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode);
     if (s != HTS_OK || n == 0) return s;
-    if (mode != HTS_GEMM_FP64) return HTS_ERR_UNSUPPORTED;
     if (n <= 2) {
         // a 1 x 1 or 2 x 2 pencil is in HT form once B is triangular: stage 0 alone
         size_t need = 0;
@@ -405,6 +520,7 @@ hts_status hts_reduce(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
     if (r > kMaxR) return HTS_ERR_UNSUPPORTED;
     int q = (p && p->q > 0) ? p->q : r;
     if (q > r) return HTS_ERR_ARG;
+    if ((s = check_emu(mode, r, q, p)) != HTS_OK) return s;
     DeviceGuard g(ctx->device);
     if (!g.ok) return HTS_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -419,7 +535,7 @@ hts_status hts_reduce(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
             return HTS_ERR_CUDA;
         ps.done(HTS_K_STAGE1, 0.0, 0.0);
     }
-    return run_stage2(ctx, n, r, A, lda, B, ldb, Qp, ldq, Zp, ldz, q, p ? p->flags : 0, work, st);
+    return run_stage2(ctx, n, r, A, lda, B, ldb, Qp, ldq, Zp, ldz, q, p ? p->flags : 0, mode, work, st);
 }
 
 hts_status hts_workspace_size_batched(int count, const int *n, const int *r, const hts_params *p, size_t *bytes)

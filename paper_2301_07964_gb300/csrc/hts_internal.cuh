@@ -16,7 +16,7 @@ struct hts_prof_state {
     int cap, used, dropped;
     cudaEvent_t *ev;     // 2 * cap events: start, end of launch i
     int *kind;
-    double *flops, *bytes;
+    double *flops, *bytes, *mma;
 };
 
 struct hts_ctx {
@@ -173,7 +173,7 @@ struct ProfScope {
     cudaStream_t st;
     int idx;
     ProfScope(hts_ctx *c, cudaStream_t s);
-    void done(int kind, double flops, double bytes);
+    void done(int kind, double flops, double bytes, double mma_flops = 0.0);
 };
 
 // Arguments of the stage-2 launches (kernels in stage2.cu).
@@ -191,13 +191,36 @@ struct GenArgs {
 };
 
 // kind 0 = A, 1 = B (Z^ reflectors on rows x < i4(k, j)), 2 = Z (Z^, all rows),
-// 3 = Q (Q^, all rows)
+// 3 = Q (Q^, all rows).  emu_rows > 0: the blocks of A and B rows that the emulated kernel
+// took (every block whose whole reflector set is pending for all rows of its tile of emu_rows
+// rows) are skipped here.
 struct ApplyArgs {
     double *M[4];
     int ld[4];
     int kind[4];
     int n, r, j1, qg;
     ReflectorSet R;
+    const int *status;
+    int emu_rows;
+};
+
+// Block formation (emu.cu): the products U^Q_k, U^Z_k of a group's reflectors per block k,
+// stored as BF16 digit planes.
+struct FormUArgs {
+    int n, r, j1, qg;
+    ReflectorSet R;
+    uint2 *planesQ, *planesZ;
+    const int *status;
+};
+
+// Emulated delayed updates (emu.cu).  kind 0 = A rows, 1 = B rows (blocks above the
+// staircase), 2 = Z rows, 3 = Q rows, 4 = A columns, 5 = B columns (left updates).
+struct EmuArgs {
+    double *M[4];
+    int ld[4];
+    int kind[4];
+    int n, r, j1, qg;
+    const uint2 *planesQ, *planesZ;
     const int *status;
 };
 
@@ -211,6 +234,11 @@ struct LeftArgs {
 };
 
 cudaError_t launch_s2_generate(const GenArgs &a, cudaStream_t st);
+cudaError_t launch_s2_form_u(const FormUArgs &a, cudaStream_t st);
+cudaError_t launch_s2_emu_apply(const EmuArgs &a, int nmat, cudaStream_t st);
+size_t emu_plane_bytes(int kdim);
+bool emu_supported(int r, int qg);
+int emu_tile_rows();
 cudaError_t launch_s2_apply_right(const ApplyArgs &a, int nmat, cudaStream_t st);
 cudaError_t launch_s2_apply_left(const LeftArgs &a, cudaStream_t st);
 cudaError_t launch_set_identity(double *M, int ld, int n, cudaStream_t st);

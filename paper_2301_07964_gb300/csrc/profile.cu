@@ -18,7 +18,7 @@ ProfScope::ProfScope(hts_ctx *c, cudaStream_t s) : ctx(c), st(s), idx(-1)
     cudaEventRecord(p.ev[2 * idx], st);
 }
 
-void ProfScope::done(int kind, double flops, double bytes)
+void ProfScope::done(int kind, double flops, double bytes, double mma_flops)
 {
     if (idx < 0) return;
     hts_prof_state &p = ctx->prof;
@@ -26,6 +26,7 @@ void ProfScope::done(int kind, double flops, double bytes)
     p.kind[idx] = kind;
     p.flops[idx] = flops;
     p.bytes[idx] = bytes;
+    p.mma[idx] = mma_flops;
 }
 
 namespace {
@@ -40,6 +41,7 @@ void prof_free(hts_prof_state &p)
     std::free(p.kind);
     std::free(p.flops);
     std::free(p.bytes);
+    std::free(p.mma);
     p = hts_prof_state{};
 }
 
@@ -79,8 +81,9 @@ hts_status hts_profile_begin(hts_ctx *ctx, int max_launches)
     p.kind = static_cast<int *>(std::calloc(max_launches, sizeof(int)));
     p.flops = static_cast<double *>(std::calloc(max_launches, sizeof(double)));
     p.bytes = static_cast<double *>(std::calloc(max_launches, sizeof(double)));
+    p.mma = static_cast<double *>(std::calloc(max_launches, sizeof(double)));
     hts_status st = HTS_OK;
-    if (!p.ev || !p.kind || !p.flops || !p.bytes) st = HTS_ERR_CUDA;
+    if (!p.ev || !p.kind || !p.flops || !p.bytes || !p.mma) st = HTS_ERR_CUDA;
     for (int i = 0; st == HTS_OK && i < 2 * max_launches; ++i)
         if (cudaEventCreate(&p.ev[i]) != cudaSuccess) st = HTS_ERR_CUDA;
     if (st != HTS_OK) prof_free(p);
@@ -109,6 +112,7 @@ hts_status hts_profile_end(hts_ctx *ctx, hts_kernel_profile out[HTS_K_NKINDS], i
         o.ms += ms;
         o.flops += p.flops[i];
         o.bytes += p.bytes[i];
+        o.mma_flops += p.mma[i];
     }
     prof_free(p);
     return st;

@@ -51,16 +51,22 @@ __global__ void __launch_bounds__(NT) k_s2_apply_right(ApplyArgs a)
     const double *Ts = (kind == 3) ? a.R.TQ : a.R.TZ;
 
     if (__ldcg(a.status) != 0) return;
-    int kstop = 0;
+    int kstop = 0, kstart = kmax;
     if (kind <= 1) {
         // rows x0.. need block k only while x0 < i4(k, j1+qg-1) = j1 + 1 + max(0, (k-1) r)
         kstop = (x0 <= j1) ? 0 : (x0 - j1 - 1) / r + 2;
-        if (kstop > kmax) return;
+        if (a.emu_rows > 0) {
+            // the emulated kernel applied blocks k > kT of this row tile
+            const int xt = imin(((x0 - 1) / a.emu_rows + 1) * a.emu_rows, n);
+            const int kT = (xt <= j1) ? -1 : qg + (xt - j1 - 1) / r;
+            kstart = imin(kstart, kT);
+        }
+        if (kstop > kstart) return;
     }
 
-    // window kmax: all w columns
+    // window kstart: all w columns
     {
-        const int c0 = j1 + kmax * r + 1;
+        const int c0 = j1 + kstart * r + 1;
         for (int e = tid; e < w * NR; e += NT) {
             const int p = e / NR, re = e % NR;
             const int c = c0 + p, xr = x0 + re;
@@ -68,7 +74,7 @@ __global__ void __launch_bounds__(NT) k_s2_apply_right(ApplyArgs a)
         }
     }
     double pre[kPrefetch];
-    for (int k = kmax; k >= kstop; --k) {
+    for (int k = kstart; k >= kstop; --k) {
         const int c0 = j1 + k * r + 1;
         for (int e = tid; e < qg * r; e += NT) {
             const int sidx = e / r, i = e % r;
