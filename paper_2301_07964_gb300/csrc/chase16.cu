@@ -1,0 +1,527 @@
+// Generate phase of stage 2 (Alg. 3) for r <= 16: the near-diagonal bulge chase of one group
+// of qg sweeps, organised around the cost of FP64 on this GPU.
+//
+// An FP64 instruction occupies the FP64 unit of its SM sub-partition for about 64 cycles
+// whether 1 or 32 lanes are active, and the four sub-partitions of an SM share little else.
+// The chase is a chain of dependent reflectors, so its length is the number of FP64
+// instructions on that chain.  The block therefore splits roles by sub-partition (warp w runs
+// on sub-partition w mod 4):
+//   warp 0        the panel: every step of the sequential chain (reflector generation, and
+//                 in the RQ the update of the next pivot row), with the lanes as columns;
+//   warps 1 .. 3  bulk updates of the current reflector (other sub-partitions, in parallel);
+//   warp 4        progress waits and global stores (no FP64);
+//   warps 5 .. 7  the band rows of A and B, held in registers (one thread per row).
+//
+// One step (k, j), sweep j waiting as in the general kernel (chase.cu) for block k+2 of sweep
+// j-1 and block k+1 of its helper:
+//   1. prefetch the pivot column segment, the block's newest B column, the earlier sweeps'
+//      left reflectors of block k with their Gram entries, the B block and the band rows;
+//   2. lazy left updates, aggregated: with w_b = tau_b u_b.x and g_ab = tau_b u_a.u_b (a < b,
+//      the Gram entries, formed by the helper blocks as each reflector appears) the
+//      coefficients of the sequential application are d_b = w_b - sum_{a<b} d_a g_ab, and
+//      x -= sum_b d_b u_b (warp 1: pivot column, warp 2: B column);
+//   3. left reflector Q^_k^j from the pivot column (panel) while the bulk warps form the
+//      B block's column dots with it; then the block update;
+//   4. RQ of the B block, last row first, with look-ahead: while the bulk warps apply
+//      reflector t to the remaining rows of W and to G, the panel applies it to the next
+//      pivot row and forms reflector t+1 from it.  RQ reflectors are scaled,
+//      c (|u|^2 I - 2 u u^T) with c a power of two, which needs a square root but no division;
+//      only the direction of G's first column is used and the scaling leaves it unchanged;
+//   5. opposite reflector Z^_k^j from G(:, 1) (panel) while the band threads form their dots
+//      with G(:, 1); then the band update, with B(i1+1:i2, i1) = 0 exactly;
+//   6. publish block k of sweep j.
+// Reflectors are stored as (u, tau) with H = I - tau u u^T, u = x - beta e_1, tau = 2/|u|^2 and
+// beta = -sign(x_1) |x| (the sign of LAPACK's dlarfg); tau = 0 is the identity.
+#include "hts_internal.cuh"
+
+namespace hts {
+
+namespace {
+
+constexpr int kM = 16;          // largest block
+constexpr int kLD = kM + 1;     // leading dimension of the shared tiles
+constexpr unsigned kFull = 0xffffffffu;
+
+// Sum over the 16 lanes of each half-warp; every lane receives its half's sum.
+__device__ __forceinline__ double sum16(double v)
+{
+    v += __shfl_xor_sync(kFull, v, 8);
+    v += __shfl_xor_sync(kFull, v, 4);
+    v += __shfl_xor_sync(kFull, v, 2);
+    v += __shfl_xor_sync(kFull, v, 1);
+    return v;
+}
+
+__device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong(v) << 1) == 0; }
+
+// nxo (sum of squares below the pivot) and alpha (pivot) far from over- and underflow;
+// tested on the exponent bits.
+__device__ __forceinline__ bool safe_sums(double nxo, double alpha)
+{
+    const int en = (__double2hiint(nxo) >> 20) & 0x7ff;
+    const int ea = (__double2hiint(alpha) >> 20) & 0x7ff;
+    return en > 60 && en < 1986 && ea < 1500;
+}
+
+// -sign(alpha) nrm, sign(0) = +1 (sign bit arithmetic).
+__device__ __forceinline__ double neg_sign_of(double alpha, double nrm)
+{
+    const int sa = __double2hiint(alpha) & 0x80000000;
+    return __hiloint2double(__double2hiint(nrm) ^ sa ^ 0x80000000, __double2loint(nrm));
+}
+
+// Householder vector of the panel lanes' x (lane c holds x_c, pivot at lane piv, entries
+// beyond len zero).  Returns u_c in the calling lane, and beta, |u|^2; `esc` receives the
+// power of two the vector was scaled by (x_used = x 2^-esc, 0 unless the sums were unsafe).
+// ident: x has no entries below the pivot (the reflector is the identity).
+__device__ __forceinline__ double panel_house(double x, int c, int piv, int len, double *beta, double *un2, int *esc,
+                                              bool *ident)
+{
+    double sq = (c < len && c != piv) ? x : 0.0;
+    double nxo = sum16(sq * sq);
+    double alpha = __shfl_sync(kFull, x, piv);
+    *esc = 0;
+    if (is_zero(nxo)) {
+        *ident = true;
+        *beta = alpha;
+        *un2 = 0.0;
+        return 0.0;
+    }
+    *ident = false;
+    if (!safe_sums(nxo, alpha)) {
+        // rare: rescale by a power of two so that the largest entry is in [1, 2)
+        double mx = (c < len) ? fabs(x) : 0.0;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, o));
+        const int e = ilogb(mx);
+        x = scalbn(x, -e);
+        *esc = e;
+        sq = (c < len && c != piv) ? x : 0.0;
+        nxo = sum16(sq * sq);
+        alpha = __shfl_sync(kFull, x, piv);
+    }
+    const double nx = fma(alpha, alpha, nxo);
+    const double nrm = nx * rsqrt(nx);
+    const double b = neg_sign_of(alpha, nrm);
+    const double up = alpha - b;
+    *beta = b;
+    *un2 = fma(up, up, nxo);
+    return (c == piv) ? up : ((c < len) ? x : 0.0);
+}
+
+// 2^-e and 2^(1-e) for the binary exponent e of a positive normal d.
+__device__ __forceinline__ void pow2_scale(double d, double *s, double *s2)
+{
+    const int eb = (__double2hiint(d) >> 20) & 0x7ff;
+    *s = __hiloint2double((2046 - eb) << 20, 0);
+    *s2 = __hiloint2double((2047 - eb) << 20, 0);
+}
+
+__device__ __forceinline__ void named_barrier(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kGenThreads) k_s2_chase16(GenArgs a)
+{
+    __shared__ double col[2 * kMaxR];      // pivot column segment
+    __shared__ double bcol[2 * kMaxR];     // newest B column segment
+    __shared__ double W[kM * kLD];         // B block (row-major), then the RQ work array
+    __shared__ double Wq[kM * kLD];        // B block after Q^ (band rows i1 .. i2 of B)
+    __shared__ double G[kM * kLD];         // accumulated right factor of the RQ (row-major)
+    __shared__ double lv[kM * kLD];        // earlier sweeps' left reflectors of block k
+    __shared__ double lt[kM];
+    __shared__ double gr[kM * kM];         // their Gram entries tau_b u_a.u_b, a < b
+    __shared__ double hu[2][kM];           // RQ reflector vectors (double buffered)
+    __shared__ double hs[2][2];            // RQ scale factors {s1, sc2}; s1 = 0: identity
+    __shared__ double pu[kM];              // current Q^ / Z^ vector
+    __shared__ double ps[2];               // {tau applied to the unscaled data, beta}
+    __shared__ double vv[kM];              // helper block: current reflector
+    __shared__ int s_abort;
+
+    const bool helper = (int)blockIdx.x >= a.qg;
+    const int s = helper ? (int)blockIdx.x - a.qg : (int)blockIdx.x;
+    const int j = a.j1 + s;
+    const int n = a.n, r = a.r, j1 = a.j1, qg = a.qg;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int kdim = a.R.kdim;
+    const int kl = nblocks_lazy(n, r, j);
+    const int kg = nblocks_gen(n, r, j);
+    const int kl_prev = s > 0 ? nblocks_lazy(n, r, j - 1) : 0;
+    double *VQs = a.R.VQ + (size_t)s * kdim * r;
+    double *VZs = a.R.VZ + (size_t)s * kdim * r;
+    double *TQs = a.R.TQ + (size_t)s * kdim;
+    double *TZs = a.R.TZ + (size_t)s * kdim;
+    double *A = a.A, *B = a.B;
+    const int lda = a.lda, ldb = a.ldb;
+    const int nlazy = j - j1;
+    const int qm = a.qmax;
+
+    for (int k = kg + tid; !helper && k < kdim; k += kGenThreads) {   // blocks this sweep does not reach
+        TQs[k] = 0.0;
+        TZs[k] = 0.0;
+    }
+    if (tid == 0) s_abort = __ldcg(a.status) != 0;   // an earlier kernel of this call failed
+    __syncthreads();
+    if (s_abort) return;
+    unsigned long long *hflags = a.flags + a.qmax;       // progress of the helper blocks
+
+    if (helper) {
+        // Rows i4 .. cr-1 of each step's band (cr = j1+kr+1, the first row any later step of
+        // the group reads), and the Gram entries of this sweep's left reflector of block k
+        // with the earlier sweeps' ones, which the later sweeps' lazy updates use.
+        for (int k = 0; k < kg; ++k) {
+            if (tid == 0) {
+                const bool ok = wait_at_least(a.flags + s, a.epoch | (unsigned long long)(k + 1), a.status, a.group, k, j) &&
+                                (s == 0 || wait_at_least(hflags + s - 1, a.epoch | (unsigned long long)(k + 2), a.status,
+                                                         a.group, k, j));
+                s_abort = !ok;
+            }
+            __syncthreads();
+            if (s_abort) return;
+            const StepGeom g = step_geom(n, r, j1, qg, k, j);
+            const int m = g.i2 - g.i1 + 1;
+            const int cr = j1 + k * r + 1;
+            const double tz = __ldcg(TZs + k);
+            if (tid < kM) vv[tid] = tid < m ? __ldcg(VZs + (size_t)k * r + tid) : 0.0;
+            // Gram column s of block k: tau_s u_a . u_s for the earlier sweeps a < s
+            if (warp == 7 && lane < s) {
+                const double tq = __ldcg(TQs + k);
+                const int ra = lane;
+                const int ma = imin(r, n - (j1 + ra + k * r)), ms = imin(r, n - (j + k * r));
+                const double *ua = a.R.VQ + ((size_t)ra * kdim + k) * r;   // rows ra .. of the segment
+                const double *us = VQs + (size_t)k * r;                      // rows s ..
+                double d0 = 0.0, d1 = 0.0;
+                const int hi = imin(ra + ma, s + ms);
+                for (int i = s; i < hi; i += 2) {
+                    d0 = fma(__ldcg(ua + i - ra), __ldcg(us + i - s), d0);
+                    if (i + 1 < hi) d1 = fma(__ldcg(ua + i + 1 - ra), __ldcg(us + i + 1 - s), d1);
+                }
+                a.gram[((size_t)k * qm + ra) * qm + s] = tq * (d0 + d1);
+            }
+            __syncthreads();
+            const int na = imax(0, imin(cr - 1, g.i3) - g.i4 + 1), nbr = imax(0, imin(cr - 1, g.i2) - g.i4 + 1);
+            if (tz != 0.0) band_rows(A, lda, B, ldb, g.i4, na, nbr, g.i1, m, tz, vv, false);
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) st_release_u64(hflags + s, a.epoch | (unsigned long long)(k + 1));
+        }
+        if (tid == 0) st_release_u64(hflags + s, a.epoch | 0xffffffffULL);
+        return;
+    }
+
+    const int c = lane & 15;   // panel lanes: column index (both half-warps hold the same data)
+    double brow[kM];           // band threads: their row
+
+    for (int k = 0; k < kl; ++k) {
+        // ---- wait until sweep j-1 has finished block k+2 (or all of its blocks), and its helper
+        //      block k+1 (its rows of block k+1 hold the upper rows of this step's B column)
+        if (tid == 128 && s > 0)
+            s_abort = !(wait_at_least(a.flags + s - 1, a.epoch | (unsigned long long)imin(k + 3, kl_prev), a.status,
+                                      a.group, k, j) &&
+                        wait_at_least(hflags + s - 1, a.epoch | (unsigned long long)(k + 2), a.status, a.group, k, j));
+        __syncthreads();
+        if (s_abort) return;
+
+        const StepGeom g = step_geom(n, r, j1, qg, k, j);
+        const bool gen = k < kg;
+        const int rlo = j1 + k * r + 1;
+        const int rhi = imin(j + (k + 1) * r, n);
+        const int L = rhi - rlo + 1;
+        const int cb = g.i1 + r - 1;
+        const bool hasb = cb <= n;
+        const int m = g.i2 - g.i1 + 1;
+        const int off = j - j1;
+        // band rows of the main block (rows >= cr = rlo; the helper takes i4 .. cr-1):
+        // A rows x0 .. i3, B rows x0 .. i1-1 above the block, then the block rows i1 .. i2
+        const int x0 = imax(g.i4, rlo);
+        const int na = gen ? imax(0, g.i3 - x0 + 1) : 0;
+        const int nbt = gen ? g.i1 - x0 : 0;
+        const int nband = gen ? na + nbt + m : 0;
+        const int bt = tid - 160;   // band thread index (warps 5 .. 7)
+
+        // ---- 1. prefetch
+        for (int i = tid; i < L; i += kGenThreads) {
+            col[i] = __ldcg(A + AT(lda, rlo + i, g.jb));
+            if (hasb) bcol[i] = __ldcg(B + AT(ldb, rlo + i, cb));
+        }
+        for (int e = tid; e < nlazy * r; e += kGenThreads) {
+            const int sh = e / r, i = e % r;
+            lv[sh * kLD + i] = (k < nblocks_gen(n, r, j1 + sh)) ? __ldcg(a.R.VQ + ((size_t)sh * kdim + k) * r + i) : 0.0;
+        }
+        for (int e = tid; e < nlazy; e += kGenThreads)
+            lt[e] = (k < nblocks_gen(n, r, j1 + e)) ? __ldcg(a.R.TQ + (size_t)e * kdim + k) : 0.0;
+        for (int e = tid; e < nlazy * nlazy; e += kGenThreads) {
+            const int ra = e / nlazy, rb = e % nlazy;
+            gr[ra * kM + rb] = (ra < rb && k < nblocks_gen(n, r, j1 + rb))
+                                   ? __ldcg(a.gram + ((size_t)k * qm + ra) * qm + rb) : 0.0;
+        }
+        if (gen) {
+            for (int e = tid; e < m * m; e += kGenThreads) {
+                const int i = e % m, cc = e / m;
+                if (!(hasb && cc == m - 1)) W[i * kLD + cc] = __ldcg(B + AT(ldb, g.i1 + i, g.i1 + cc));
+                G[i * kLD + cc] = (i == cc) ? 1.0 : 0.0;
+            }
+        }
+        if (bt >= 0 && bt < na + nbt) {
+            const bool isA = bt < na;
+            const int x = x0 + (isA ? bt : bt - na);
+            const double *src = isA ? A + AT(lda, x, g.i1) : B + AT(ldb, x, g.i1);
+            const size_t ld = isA ? (size_t)lda : (size_t)ldb;
+#pragma unroll
+            for (int cc = 0; cc < kM; ++cc) brow[cc] = (cc < m) ? __ldcg(src + cc * ld) : 0.0;
+        }
+        __syncthreads();
+
+        // ---- 2. lazy left updates (warp 1: pivot column, warp 2: B column)
+        if (nlazy > 0 && L > 0 && (warp == 1 || (warp == 2 && hasb))) {
+            double *seg = (warp == 1) ? col : bcol;
+            const int ns = nlazy;
+            double wv = 0.0;
+            if (lane < ns) {
+                const int mb = imin(r, n - (j1 + lane + k * r));
+                const double *ub = lv + lane * kLD;
+                const double *xs = seg + lane;
+                double d0 = 0.0, d1 = 0.0;
+                for (int i = 0; i < mb; i += 2) {
+                    d0 = fma(ub[i], xs[i], d0);
+                    if (i + 1 < mb) d1 = fma(ub[i + 1], xs[i + 1], d1);
+                }
+                wv = lt[lane] * (d0 + d1);
+            }
+            for (int ra = 0; ra + 1 < ns; ++ra) {
+                const double da = __shfl_sync(kFull, wv, ra);
+                if (lane > ra && lane < ns) wv = fma(-da, gr[ra * kM + lane], wv);
+            }
+            // lane b holds d_b; lane i: x_i -= sum_b d_b u_b(i - b)  (L <= 31)
+            double e0 = 0.0, e1 = 0.0;
+            for (int rb = 0; rb < ns; ++rb) {
+                const double db = __shfl_sync(kFull, wv, rb);
+                const int mb = imin(r, n - (j1 + rb + k * r));
+                const int i0 = lane - rb;
+                const double u = (i0 >= 0 && i0 < mb) ? lv[rb * kLD + i0] : 0.0;
+                if (rb & 1) e1 = fma(db, u, e1);
+                else e0 = fma(db, u, e0);
+            }
+            if (lane < L) seg[lane] -= e0 + e1;
+        }
+        __syncthreads();
+
+        if (gen) {
+            // ---- 3. left reflector Q^ from col[off .. off+m-1] (panel); column dots (warps 1, 2)
+            double pdot = 0.0, y[4], y0 = 0.0;
+            const int qcol = (warp - 1) * 8 + (lane >> 2), qsub = lane & 3;   // warps 1, 2: column, row set
+            const bool qown = (warp == 1 || warp == 2) && qcol < m;
+            const bool qfromb = hasb && qcol == m - 1;
+            if (warp == 0) {
+                const double x = (c < m) ? col[off + c] : 0.0;
+                double beta, un2;
+                int esc;
+                bool ident;
+                const double u = panel_house(x, c, 0, m, &beta, &un2, &esc, &ident);
+                const double tau = ident ? 0.0 : 2.0 * __drcp_rn(un2);
+                if (lane < kM) pu[lane] = u;
+                if (lane == 0) {
+                    ps[0] = ident ? 0.0 : (esc ? scalbn(tau, -esc) : tau);
+                    ps[1] = ident ? beta : (esc ? scalbn(beta, esc) : beta);
+                    TQs[k] = tau;
+                }
+                if (lane < r) VQs[(size_t)k * r + lane] = (!ident && lane < m) ? u : 0.0;
+            } else if (warp == 1 || warp == 2) {
+                // every lane of both warps takes part in the shuffles; lanes without a column
+                // contribute zeros
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int i = qsub + 4 * e;
+                    y[e] = (qown && i < m) ? (qfromb ? bcol[off + i] : W[i * kLD + qcol]) : 0.0;
+                    if (qown && i < m) pdot = fma(y[e], col[off + i], pdot);
+                }
+                pdot += __shfl_xor_sync(kFull, pdot, 1);
+                pdot += __shfl_xor_sync(kFull, pdot, 2);
+                if (qown) y0 = qfromb ? bcol[off] : W[qcol];   // read before any lane rewrites row 0
+            }
+            __syncthreads();
+            if (qown) {
+                const double tau = ps[0], beta = ps[1];
+                const double cf = tau != 0.0 ? fma(-beta, y0, pdot) * tau : 0.0;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int i = qsub + 4 * e;
+                    if (i < m) {
+                        const double v = fma(-cf, pu[i], y[e]);
+                        W[i * kLD + qcol] = v;
+                        Wq[i * kLD + qcol] = v;
+                    }
+                }
+            }
+            if (warp == 0 && ps[0] != 0.0 && lane < m) col[off + lane] = (lane == 0) ? ps[1] : 0.0;
+            __syncthreads();
+        }
+
+        // pivot and B column segments are final (the B column's block rows are rewritten with
+        // the band); warp 4 stores them while the RQ runs
+        if (warp == 4)
+            for (int i = lane; i < L; i += 32) {
+                A[AT(lda, rlo + i, g.jb)] = col[i];
+                if (hasb) B[AT(ldb, rlo + i, cb)] = bcol[i];
+            }
+
+        // ---- 4. RQ of the B block with look-ahead (warps 0 .. 3)
+        if (gen && m >= 2 && warp < 4) {
+            double u = 0.0, s1 = 0.0, sc2 = 0.0;   // panel: current reflector
+            if (warp == 0) {
+                const int piv = m - 1;
+                const double x = (c <= piv) ? W[piv * kLD + c] : 0.0;
+                double beta, un2;
+                int esc;
+                bool ident;
+                u = panel_house(x, c, piv, piv + 1, &beta, &un2, &esc, &ident);
+                if (!ident) {
+                    double sc;
+                    pow2_scale(un2, &sc, &sc2);
+                    s1 = un2 * sc;
+                }
+                if (lane < kM) hu[0][lane] = u;
+                if (lane == 0) {
+                    hs[0][0] = s1;
+                    hs[0][1] = sc2;
+                }
+            }
+            named_barrier(1, 128);
+            for (int t = 0; t + 1 < m; ++t) {
+                const int piv = m - 1 - t, cur = t & 1;
+                if (warp == 0) {
+                    if (piv >= 2) {
+                        // next pivot row: apply reflector t, then form reflector t+1 from it
+                        double y = (c <= piv) ? W[(piv - 1) * kLD + c] : 0.0;
+                        if (s1 != 0.0) {
+                            const double cf = sum16(y * u) * sc2;
+                            y = fma(-cf, u, s1 * y);
+                        }
+                        double beta, un2;
+                        int esc;
+                        bool ident;
+                        u = panel_house(y, c, piv - 1, piv, &beta, &un2, &esc, &ident);
+                        s1 = 0.0;
+                        if (!ident) {
+                            double sc;
+                            pow2_scale(un2, &sc, &sc2);
+                            s1 = un2 * sc;
+                        }
+                        if (lane < kM) hu[cur ^ 1][lane] = u;
+                        if (lane == 0) {
+                            hs[cur ^ 1][0] = s1;
+                            hs[cur ^ 1][1] = sc2;
+                        }
+                    }
+                } else {
+                    // bulk: W rows 0 .. piv-2 and G rows 0 .. m-1, three lanes per row
+                    const double bs1 = hs[cur][0];
+                    const int nrows = (piv - 1) + m;
+                    const int rho = (warp - 1) * 10 + lane / 3, sub = lane % 3;
+                    const bool own = lane < 30 && rho < nrows;
+                    if (bs1 != 0.0) {
+                        double *rowp = (rho < piv - 1) ? &W[rho * kLD] : &G[(rho - (piv - 1)) * kLD];
+                        double yv[6], uv[6];
+                        double p = 0.0;
+#pragma unroll
+                        for (int e = 0; e < 6; ++e) {
+                            const int cc = sub + 3 * e;
+                            const bool in = own && cc <= piv;
+                            yv[e] = in ? rowp[cc] : 0.0;
+                            uv[e] = in ? hu[cur][cc] : 0.0;
+                            p = fma(yv[e], uv[e], p);
+                        }
+                        const int base = lane - sub;
+                        const double p1 = __shfl_sync(kFull, p, (base + 1) & 31);
+                        const double p2 = __shfl_sync(kFull, p, (base + 2) & 31);
+                        const double p0 = __shfl_sync(kFull, p, base & 31);
+                        const double cf = (p0 + p1 + p2) * hs[cur][1];
+                        if (own) {
+#pragma unroll
+                            for (int e = 0; e < 6; ++e) {
+                                const int cc = sub + 3 * e;
+                                if (cc <= piv) rowp[cc] = fma(-cf, uv[e], bs1 * yv[e]);
+                            }
+                        }
+                    }
+                }
+                named_barrier(1, 128);
+            }
+        }
+        __syncthreads();
+
+        if (gen) {
+            // ---- 5. opposite reflector Z^ from G(:, 1) (panel); band dots (warps 5 .. 7)
+            double p = 0.0;
+            const bool band = bt >= 0 && bt < nband;
+            const bool isA = bt < na;
+            const int xrow = isA ? x0 + bt : x0 + (bt - na);
+            if (warp == 0) {
+                const double x = (c < m) ? G[c * kLD] : 0.0;
+                double beta, un2;
+                int esc;
+                bool ident;
+                const double u = panel_house(x, c, 0, m, &beta, &un2, &esc, &ident);
+                const double tau = ident ? 0.0 : 2.0 * __drcp_rn(un2);
+                if (lane < kM) pu[lane] = u;
+                if (lane == 0) {
+                    ps[0] = ident ? 0.0 : (esc ? scalbn(tau, -esc) : tau);
+                    ps[1] = ident ? beta : (esc ? scalbn(beta, esc) : beta);
+                    TZs[k] = tau;
+                }
+                if (lane < r) VZs[(size_t)k * r + lane] = (!ident && lane < m) ? u : 0.0;
+            } else if (band) {
+                if (bt >= na + nbt) {
+                    const int bi = bt - na - nbt;
+#pragma unroll
+                    for (int cc = 0; cc < kM; ++cc) brow[cc] = (cc < m) ? Wq[bi * kLD + cc] : 0.0;
+                } else if (!isA && hasb) {
+                    // the B column cb above the block carries the lazy updates of step 2
+                    const double v = bcol[xrow - rlo];
+#pragma unroll
+                    for (int cc = 0; cc < kM; ++cc)
+                        if (cc == m - 1) brow[cc] = v;
+                }
+                double p0 = 0.0, p1 = 0.0;
+#pragma unroll
+                for (int cc = 0; cc < kM; cc += 2) {
+                    if (cc < m) p0 = fma(brow[cc], G[cc * kLD], p0);
+                    if (cc + 1 < m) p1 = fma(brow[cc + 1], G[(cc + 1) * kLD], p1);
+                }
+                p = p0 + p1;
+            }
+            if (warp == 0 || warp >= 5) named_barrier(2, 128);
+            if (band) {
+                const double tau = ps[0], beta = ps[1];
+                if (tau != 0.0) {
+                    const double cf = fma(-beta, brow[0], p) * tau;
+#pragma unroll
+                    for (int cc = 0; cc < kM; ++cc) brow[cc] = fma(-cf, pu[cc], brow[cc]);
+                }
+                if (!isA && xrow > g.i1) brow[0] = 0.0;   // the reduced column of the B block
+                double *dst = isA ? A + AT(lda, xrow, g.i1) : B + AT(ldb, xrow, g.i1);
+                const size_t ld = isA ? (size_t)lda : (size_t)ldb;
+#pragma unroll
+                for (int cc = 0; cc < kM; ++cc)
+                    if (cc < m) dst[cc * ld] = brow[cc];
+            }
+        }
+
+        // ---- 6. publish block k of this sweep
+        __threadfence();
+        __syncthreads();
+        if (tid == 0 && !(a.stall && s == 0))
+            st_release_u64(a.flags + s, a.epoch | (unsigned long long)(k + 1));
+    }
+}
+
+cudaError_t launch_s2_chase16(const GenArgs &a, cudaStream_t st)
+{
+    void *args[] = {(void *)&a};
+    return cudaLaunchCooperativeKernel((const void *)k_s2_chase16, dim3(2 * a.qg), dim3(kGenThreads), args, 0, st);
+}
+
+}  // namespace hts

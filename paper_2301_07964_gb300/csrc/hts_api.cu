@@ -32,7 +32,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // blocks' reflector products (one plane set per reflector set).
 struct S2Layout {
     int kdim, qmax;
-    size_t off_vq[2], off_tq[2], off_vz[2], off_tz[2], off_flags, total_fp64;
+    size_t off_vq[2], off_tq[2], off_vz[2], off_tz[2], off_gram[2], off_flags, total_fp64;
     size_t off_pq[2], off_pz[2], total;
 };
 
@@ -49,6 +49,7 @@ S2Layout s2_layout(int n, int r)
         L.off_tq[b] = o; o = align_up(o + nt, 256);
         L.off_vz[b] = o; o = align_up(o + nv, 256);
         L.off_tz[b] = o; o = align_up(o + nt, 256);
+        L.off_gram[b] = o; o = align_up(o + (size_t)L.kdim * L.qmax * L.qmax * sizeof(double), 256);
     }
     L.off_flags = o; o = align_up(o + 2 * (size_t)L.qmax * sizeof(unsigned long long), 256);
     L.total_fp64 = o;
@@ -243,12 +244,14 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         ga.A = A; ga.B = B; ga.lda = lda; ga.ldb = ldb;
         ga.n = n; ga.r = r; ga.j1 = j1; ga.qg = qg; ga.group = group;
         ga.R = R[set]; ga.flags = fl; ga.qmax = L.qmax;
+        ga.gram = reinterpret_cast<double *>(w + L.off_gram[set]);
         ga.epoch = (unsigned long long)(group + 1) << 32;
         ga.status = ctx->d_status;
         ga.stall = (flags & HTS_FLAG_TEST_STALL) ? 1 : 0;
         {
             ProfScope ps(ctx, st);
-            if ((e = launch_s2_generate(ga, st)) != cudaSuccess) return HTS_ERR_CUDA;
+            e = (r <= 16) ? launch_s2_chase16(ga, st) : launch_s2_generate(ga, st);
+            if (e != cudaSuccess) return HTS_ERR_CUDA;
             ps.done(HTS_K_GENERATE, gc.f_gen, gc.b_gen);
         }
 

@@ -185,6 +185,8 @@ struct GenArgs {
     ReflectorSet R;
     unsigned long long *flags;   // progress words: [0, qmax) main blocks, [qmax, 2 qmax) helpers
     int qmax;
+    double *gram;                // tau_b u_a.u_b of the group's left reflectors per block:
+                                 // gram[(k * qmax + a) * qmax + b], a < b (written by helpers)
     unsigned long long epoch;    // (group + 1) << 32
     int *status;
     int stall;                   // fault injection: slot 0 never publishes (tests only)
@@ -234,6 +236,7 @@ struct LeftArgs {
 };
 
 cudaError_t launch_s2_generate(const GenArgs &a, cudaStream_t st);
+cudaError_t launch_s2_chase16(const GenArgs &a, cudaStream_t st);
 cudaError_t launch_s2_form_u(const FormUArgs &a, cudaStream_t st);
 cudaError_t launch_s2_emu_apply(const EmuArgs &a, int nmat, cudaStream_t st);
 size_t emu_plane_bytes(int kdim);
@@ -293,5 +296,53 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+
+// Bounded wait (one thread) until *flag >= need; on expiry records HTS_ERR_TIMEOUT.
+__device__ __forceinline__ bool wait_at_least(const unsigned long long *flag, unsigned long long need, int *status, int group, int k,
+                              int j)
+{
+    const unsigned long long t0 = globaltimer_ns();
+    long long polls = 0;
+    while (ld_acquire_u64(flag) < need) {
+        if (++polls > kSpinLimit || globaltimer_ns() - t0 > kWaitLimitNs) {
+            record_error(status, HTS_ERR_TIMEOUT, 0, group, k, j);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Rows x0 .. x0+na-1 of A and x0 .. x0+nbr-1 of B, columns i1 .. i1+m-1, times Z^ = I - tz v v^T
+// (one thread per row).  zero_first: B(x, i1) := 0 exactly for x > i1 (the reduced column).
+__device__ __forceinline__ void band_rows(double *A, int lda, double *B, int ldb, int x0, int na, int nbr, int i1, int m, double tz,
+                          const double *vv, bool zero_first)
+{
+    for (int t = threadIdx.x; t < na + nbr; t += kGenThreads) {
+        const bool isA = t < na;
+        const int x = x0 + (isA ? t : t - na);
+        double *base = isA ? A : B;
+        const int ld = isA ? lda : ldb;
+        double rowv[kMaxR];
+        double d0 = 0.0, d1 = 0.0;
+#pragma unroll
+        for (int c = 0; c < kMaxR; ++c) {
+            if (c < m) {
+                rowv[c] = __ldcg(base + AT(ld, x, i1 + c));
+                if (c & 1) d1 += rowv[c] * vv[c];
+                else d0 += rowv[c] * vv[c];
+            }
+        }
+        const double d = (d0 + d1) * tz;
+#pragma unroll
+        for (int c = 0; c < kMaxR; ++c) {
+            if (c < m) {
+                double val = rowv[c] - d * vv[c];
+                if (zero_first && !isA && c == 0 && x > i1) val = 0.0;
+                base[AT(ld, x, i1 + c)] = val;
+            }
+        }
+    }
+}
+
 
 }  // namespace hts
