@@ -9,10 +9,15 @@ r-Hessenberg-triangular pencil (A with 16 subdiagonals, B the R factor of a Gaus
 with Q and Z accumulated.  The inputs (1 GiB for A and B) are larger than L2, and each step
 restores A and B from pristine device copies before the timed call.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mode fp64|emu]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mode emu|fp64]
 
+``--mode`` selects the arithmetic of the delayed updates: ``emu`` (default) forms each block's
+reflector product and applies it in FP64 emulated on the BF16 tensor cores, ``fp64`` applies
+the reflectors one at a time in native FP64; the chase is native FP64 in both.
 ``--impl reference`` times the CPU oracle (Alg. 2 in plain C, OpenMP) on the host cores:
 each step is a bounded sample (the first sweeps) of the same workload.
+``--workload reduce|batch`` time the full reduction and the many-pencil case (supplementary
+lines); ``--workload probe`` runs two untimed stage-2 calls for profiler captures.
 """
 from __future__ import annotations
 
@@ -36,8 +41,9 @@ UNIT = "GFLOP/s"
 N_DEFAULT, R_DEFAULT, SEED = 8192, 16, 4
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-KERNEL_SOURCES = {"k_s2_generate": "stage2.cu", "k_s2_apply_right": "stage2.cu",
-                  "k_s2_apply_left": "stage2.cu"}
+KERNEL_SOURCES = {"k_s2_generate": "chase.cu", "k_s2_chase16": "chase16.cu", "k_s2_apply_right": "stage2.cu",
+                  "k_s2_apply_left": "stage2.cu", "k_s2_emu_apply_right": "emu.cu", "k_s2_emu_apply_left": "emu.cu",
+                  "k_s2_emu_apply_qz": "emu.cu", "k_s2_form_u": "emu.cu"}
 
 
 def paper_flops(n):
@@ -288,6 +294,8 @@ def run_ours(args, n, r):
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     prof, dropped = b.hts_profile_end(red.ctx)
+    if r <= 16 and "k_s2_generate" in prof:   # the chase kernel for r <= 16
+        prof["k_s2_chase16"] = prof.pop("k_s2_generate")
     st, info = red.sync_status()
     if st != b.HTS_OK:
         raise SystemExit("device error during timed steps: %s %s" % (b.status_string(st), info))
@@ -466,6 +474,33 @@ def run_reduce(args, n, r):
     return 0
 
 
+def run_probe(args, n, r):
+    """Two untimed stage-2 calls on the metric's pencil family at size n, for profiler
+    captures of single launches (no timing, no output besides a status line)."""
+    import torch
+    from paper_2301_07964_gb300 import binding as b
+    from paper_2301_07964_gb300 import build
+    from paper_2301_07964_gb300.device import Reducer, colmajor_empty, to_device
+    from paper_2301_07964_gb300.inputs import random_rht_pencil
+    build.build()
+    b.load()
+    q = args.q or r
+    mode = b.HTS_GEMM_FP64 if args.mode == "fp64" else b.HTS_GEMM_EMU_BF16
+    A, B = random_rht_pencil(n, r, SEED)
+    red = Reducer(0)
+    for _ in range(2):
+        dA, dB = to_device(A), to_device(B)
+        dQ, dZ = colmajor_empty(n), colmajor_empty(n)
+        red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, mode=mode)
+        st, info = red.sync_status()
+        if st != b.HTS_OK:
+            raise SystemExit("device error: %s %s" % (b.status_string(st), info))
+    torch.cuda.synchronize()
+    red.close()
+    print(json.dumps({"workload": "probe", "n": n, "r": r, "q": q, "mode": args.mode, "status": "ok"}))
+    return 0
+
+
 def run_batch(args):
     """4096 pencils, n uniform in [32, 512], r = min(8, n // 8), A, B iid N(0, 1), full
     reduction with Q and Z in one hts_reduce_batched launch."""
@@ -529,7 +564,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["fp64", "emu"], default="fp64")
+    ap.add_argument("--mode", choices=["fp64", "emu"], default="emu")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--r", type=int, default=R_DEFAULT)
     ap.add_argument("--q", type=int, default=0)
@@ -538,7 +573,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-sweeps", type=int, default=24)
-    ap.add_argument("--workload", choices=["stage2", "reduce", "batch"], default="stage2")
+    ap.add_argument("--workload", choices=["stage2", "reduce", "batch", "probe"], default="stage2")
     ap.add_argument("--ill", action="store_true", help="reduce: ill-conditioned B")
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--count", type=int, default=4096)
@@ -547,6 +582,8 @@ def main():
         return run_reduce(args, args.n, args.r)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "probe":
+        return run_probe(args, args.n, args.r)
     if args.impl == "reference":
         return run_reference(args, args.n, args.r)
     return run_ours(args, args.n, args.r)

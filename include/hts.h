@@ -140,7 +140,7 @@ hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r,
  *  - Scratch lives in one fixed 8 MiB array compiled into the library; every GPU that loads
  *    the library holds it until the process exits.  Sizes whose workspace
  *    (hts_workspace_size) exceeds 8 MiB are rejected with HTS_ERR_WORKSPACE before anything
- *    runs (r = 16 allows n up to about 15000, r = 32 up to about 7800).
+ *    runs (native mode: r = 16 allows n up to about 10400, r = 32 up to about 7900).
  *  - The call allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  *    with that device current); make that first call before any stream capture.

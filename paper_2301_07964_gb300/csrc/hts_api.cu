@@ -49,7 +49,8 @@ S2Layout s2_layout(int n, int r)
         L.off_tq[b] = o; o = align_up(o + nt, 256);
         L.off_vz[b] = o; o = align_up(o + nv, 256);
         L.off_tz[b] = o; o = align_up(o + nt, 256);
-        L.off_gram[b] = o; o = align_up(o + (size_t)L.kdim * L.qmax * L.qmax * sizeof(double), 256);
+        L.off_gram[b] = o;   // the Gram entries are used by the r <= 16 chase only
+        if (r <= 16) o = align_up(o + (size_t)L.kdim * L.qmax * L.qmax * sizeof(double), 256);
     }
     L.off_flags = o; o = align_up(o + 2 * (size_t)L.qmax * sizeof(unsigned long long), 256);
     L.total_fp64 = o;
