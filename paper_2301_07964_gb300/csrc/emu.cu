@@ -32,7 +32,7 @@ constexpr int kDigits = 8;                 // balanced base-256 digits per opera
 constexpr int kTopLevel = 9;               // digit pairs with i + t <= 9 are formed
 constexpr int kPlaneWords = kDigits * 2 * 4 * 32;   // uint2 words of one U_k (16 KiB)
 constexpr int kUnitU = -61;                // U_k entries as integers round(u 2^61)
-constexpr int kEmuWarps = 4;               // warps per apply block
+constexpr int kEmuWarps = 4;               // 16-line slabs per apply block
 constexpr int kEmuRows = 16 * kEmuWarps;   // rows (or columns) per apply block
 constexpr int kZeroExp = -4000;            // "exponent" of a zero value
 
@@ -137,6 +137,11 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+__device__ __forceinline__ void named_barrier(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
@@ -195,21 +200,242 @@ __global__ void __launch_bounds__(128) k_s2_form_u(FormUArgs a)
 }
 
 // ---------------------------------------------------------------------------------------
-// Emulated delayed update.  Each warp owns 16 lines (rows of X for the right updates,
-// columns of X for the left updates) and a window of 32 positions (window index p = column
-// c0 + p, or row R0 + p, with c0 = R0 = j1 + k r + 1).  Lane 4 g + c holds lines g and g + 8
-// at positions 16 kt + 8 h + 2 c + {0, 1} (kt, h in {0, 1}): exactly the A-operand positions
-// of mma.m16n8k16 and the result positions of its accumulator, so a window's result feeds
-// the next window without data movement (positions p < w - r move to p + r, i.e. kt 0 -> 1;
-// this needs r = 16).
+// Emulated delayed update.  A block owns 64 lines (rows of X for the right updates, columns
+// of X for the left updates) in four slabs of 16, and each slab's window of 32 positions
+// (window index p = column c0 + p, or row R0 + p, with c0 = R0 = j1 + k r + 1).  Two warps
+// share a slab: half 0 holds positions 0..15 (operand k-tile 0), half 1 positions 16..31.
+// Lane 4 g + c holds lines g and g + 8 at positions 16 kt + 8 h + 2 c + {0, 1}: exactly the
+// A-operand positions of mma.m16n8k16 and the result positions of its accumulator.  Per
+// block k of the group:
+//   half 0: the scale of each line (its largest entry over the new columns and the carried
+//           positions), hands the carry (last window's positions 0 .. w-r-1, which become
+//           16 .. 16+w-r-1) and the scales to half 1, and loads the next window's new columns;
+//   both:   digits of their own k-tile, exchanged through shared memory; products for their
+//           own two n-tiles (half 0: output positions 0..15, half 1: 16..31); results;
+//   half 1: stores its positions (they leave the window); half 0 keeps its positions as the
+//           next carry (all positions are stored after the last block).
+// The slide by r = 16 positions is one k-tile, which is why this kernel needs r = 16.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kEmuWarps * 32) k_s2_emu_apply(EmuArgs a)
+constexpr int kEmuThreads = 64 * kEmuWarps;   // two warps per 16-line slab
+
+struct EmuSmem {
+    uint2 planes[2][kPlaneWords];           // U digit planes of blocks k and k-1
+    uint4 dig[kEmuWarps][2][kDigits][32];   // A-operand digits of each half, [slab][half][t][lane]
+    long long carry[kEmuWarps][8][32];      // carried window positions, [slab][slot][lane]
+    int unit[kEmuWarps][2][32];             // scales of the two lines of each lane
+};
+
+template <int HALF>
+__device__ __forceinline__ void emu_worker(const EmuArgs &a, EmuSmem &S, int kind, double *X, size_t ld,
+                                           const uint2 *P, int l0, int kbeg, int kend)
 {
-    __shared__ __align__(16) uint2 planes[2][kPlaneWords];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, slab = (tid >> 5) >> 1;
     const int g = lane >> 2, c = lane & 3;
     const int n = a.n, r = a.r, j1 = a.j1, qg = a.qg;
     const int w = r + qg - 1;
+    const int jl = j1 + qg - 1;
+    const bool left = kind >= 4;
+    const int bar = 1 + slab;
+    const int lineA = l0 + slab * 16 + g, lineB = lineA + 8;   // lines of rr = 0, 1
+    auto addr = [=](int ln, int p, int k) -> double * {
+        const int pos = j1 + k * r + 1 + p;   // matrix column (right) or row (left)
+        return left ? X + (size_t)(pos - 1) + (size_t)(ln - 1) * ld : X + (size_t)(ln - 1) + (size_t)(pos - 1) * ld;
+    };
+    auto valid = [=](int ln, int p, int k) -> bool { return ln <= n && p < w && j1 + k * r + 1 + p <= n; };
+
+    double dv[2][2][2];        // half 0: FP64 values entering at positions 8 h + 2 c + pair
+    long long xc[2][2][2];     // half 0: carried positions (the next window's k-tile 1)
+    int uc[2] = {0, 0};        // their scales
+    if (HALF == 0) {
+        // first window: positions of k-tile 1 become the carry at their own scale
+        int em[2] = {kZeroExp, kZeroExp};
+        double v1[2][2][2];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                    const int ln = rr ? lineB : lineA;
+                    const int p = 8 * h + 2 * c + pr;
+                    dv[rr][h][pr] = valid(ln, p, kbeg) ? *addr(ln, p, kbeg) : 0.0;
+                    v1[rr][h][pr] = valid(ln, p + 16, kbeg) ? *addr(ln, p + 16, kbeg) : 0.0;
+                    em[rr] = imax(em[rr], exp_of_f64(v1[rr][h][pr]));
+                }
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            em[rr] = imax(em[rr], __shfl_xor_sync(0xffffffffu, em[rr], 1));
+            em[rr] = imax(em[rr], __shfl_xor_sync(0xffffffffu, em[rr], 2));
+            uc[rr] = (em[rr] == kZeroExp ? 0 : em[rr] + 2) - 64;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) xc[rr][h][pr] = f64_to_fixed(v1[rr][h][pr], uc[rr]);
+        }
+    }
+
+    for (int k = kbeg; k >= kend; --k) {
+        const bool last = (k == kend);
+        const int buf = (kbeg - k) & 1;
+        // next block's planes (all threads)
+        if (!last) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(P + (size_t)(k - 1) * kPlaneWords);
+            uint4 *dst = reinterpret_cast<uint4 *>(S.planes[buf ^ 1]);
+            for (int e = tid; e < kPlaneWords / 2; e += kEmuThreads) cp_async16(dst + e, src + e);
+        }
+        cp_async_commit();
+
+        // ---- scales and carry (half 0 -> half 1)
+        long long xv[2][2][2];   // this half's window positions in units 2^ua
+        int ua[2];
+        if (HALF == 0) {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                int em = kZeroExp;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int pr = 0; pr < 2; ++pr) {
+                        em = imax(em, exp_of_f64(dv[rr][h][pr]));
+                        em = imax(em, exp_of_fixed(xc[rr][h][pr], uc[rr]));
+                    }
+                em = imax(em, __shfl_xor_sync(0xffffffffu, em, 1));
+                em = imax(em, __shfl_xor_sync(0xffffffffu, em, 2));
+                ua[rr] = (em == kZeroExp ? 0 : em + 2) - 64;   // |x| < 2^62
+                S.unit[slab][rr][lane] = ua[rr];
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int pr = 0; pr < 2; ++pr) {
+                        S.carry[slab][(rr * 2 + h) * 2 + pr][lane] = refix(xc[rr][h][pr], uc[rr], ua[rr]);
+                        xv[rr][h][pr] = f64_to_fixed(dv[rr][h][pr], ua[rr]);
+                    }
+            }
+        }
+        named_barrier(bar, 64);
+        if (HALF == 1) {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                ua[rr] = S.unit[slab][rr][lane];
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int pr = 0; pr < 2; ++pr) xv[rr][h][pr] = S.carry[slab][(rr * 2 + h) * 2 + pr][lane];
+            }
+        } else {
+            // the next window's new columns (positions 0 .. r-1)
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int pr = 0; pr < 2; ++pr) {
+                        const int ln = rr ? lineB : lineA;
+                        const int p = 8 * h + 2 * c + pr;
+                        dv[rr][h][pr] = (!last && valid(ln, p, k - 1)) ? *addr(ln, p, k - 1) : 0.0;
+                    }
+        }
+
+        // ---- digits of this half's k-tile, exchanged with the other half
+        unsigned af[kDigits][2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                unsigned d0[kDigits], d1[kDigits];
+                digits_bf16(xv[rr][h][0], d0);
+                digits_bf16(xv[rr][h][1], d1);
+#pragma unroll
+                for (int t = 0; t < kDigits; ++t) af[t][HALF][2 * h + rr] = pack_bf16(d0[t], d1[t]);
+            }
+#pragma unroll
+        for (int t = 0; t < kDigits; ++t)
+            S.dig[slab][HALF][t][lane] = make_uint4(af[t][HALF][0], af[t][HALF][1], af[t][HALF][2], af[t][HALF][3]);
+        named_barrier(bar, 64);
+#pragma unroll
+        for (int t = 0; t < kDigits; ++t) {
+            const uint4 o = S.dig[slab][HALF ^ 1][t][lane];
+            af[t][HALF ^ 1][0] = o.x;
+            af[t][HALF ^ 1][1] = o.y;
+            af[t][HALF ^ 1][2] = o.z;
+            af[t][HALF ^ 1][3] = o.w;
+        }
+
+        // ---- line activity (left updates: columns right of the cut of block k)
+        bool act0 = true, act1 = true;
+        if (left) {
+            const int cut = (kind == 5) ? imin(jl + (k + 1) * r, n) : jl + imax(0, (k - 1) * r + 1);
+            act0 = lineA > cut;
+            act1 = lineB > cut;
+        }
+
+        cp_async_wait<1>();
+        __syncthreads();
+        const uint2 *pl = S.planes[buf];
+
+        // ---- products for this half's two n-tiles; results replace xv
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int nt = 2 * HALF + h;
+            float acc[kTopLevel - 1][4];
+#pragma unroll
+            for (int d = 0; d < kTopLevel - 1; ++d)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[d][e] = 0.0f;
+#pragma unroll
+            for (int t = 0; t < kDigits; ++t) {
+                const uint2 b0 = pl[((t * 2 + 0) * 4 + nt) * 32 + lane];
+                const uint2 b1 = pl[((t * 2 + 1) * 4 + nt) * 32 + lane];
+#pragma unroll
+                for (int i = 0; i < kDigits; ++i) {
+                    if (i + t + 2 <= kTopLevel) {   // level (i+1) + (t+1)
+                        mma_bf16(acc[i + t], af[i][0], b0.x, b0.y);
+                        mma_bf16(acc[i + t], af[i][1], b1.x, b1.y);
+                    }
+                }
+            }
+            // levels 2..9 -> one integer in units 2^(ua + 3): level L weighs 2^(8 (8 - L))
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c2 = f32_exact_int(acc[0][e]), c3 = f32_exact_int(acc[1][e]);
+                const int c4 = f32_exact_int(acc[2][e]), c5 = f32_exact_int(acc[3][e]);
+                const int c6 = f32_exact_int(acc[4][e]), c7 = f32_exact_int(acc[5][e]);
+                const int c8 = f32_exact_int(acc[6][e]), c9 = f32_exact_int(acc[7][e]);
+                const int lo = (c7 << 8) + c8 + ((c9 + 128) >> 8);
+                const int mid = (c5 << 8) + c6;
+                const long long hi = ((long long)c2 << 16) + (long long)((c3 << 8) + c4);
+                const long long val = (hi << 32) + ((long long)mid << 16) + (long long)lo;
+                const int rr = e >> 1, pr = e & 1;
+                const bool act = rr ? act1 : act0;
+                xv[rr][h][pr] = act ? val : refix(xv[rr][h][pr], ua[rr], ua[rr] + 3);
+            }
+        }
+        __syncthreads();   // planes[buf] is refilled by the next iteration's copy
+
+        // ---- positions leaving the window; half 0 keeps the carry
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int ln = rr ? lineB : lineA;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                    const int p = 16 * HALF + 8 * h + 2 * c + pr;
+                    if ((last || p >= w - r) && valid(ln, p, k))
+                        *addr(ln, p, k) = fixed_to_f64(xv[rr][h][pr], ua[rr] + 3);
+                    if (HALF == 0) xc[rr][h][pr] = (p < w - r) ? xv[rr][h][pr] : 0;
+                }
+            uc[rr] = ua[rr] + 3;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kEmuThreads) k_s2_emu_apply(EmuArgs a)
+{
+    extern __shared__ __align__(16) unsigned char emu_smem[];
+    EmuSmem &S = *reinterpret_cast<EmuSmem *>(emu_smem);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int n = a.n, r = a.r, j1 = a.j1, qg = a.qg;
     const int mi = blockIdx.y;
     const int kind = a.kind[mi];
     const bool left = kind >= 4;
@@ -240,193 +466,15 @@ __global__ void __launch_bounds__(kEmuWarps * 32) k_s2_emu_apply(EmuArgs a)
     }
     if (kbeg < kend || l0 > n) return;
 
-    const int lineA = l0 + warp * 16 + g, lineB = lineA + 8;   // lines of rr = 0, 1
-    auto addr = [=](int ln, int p, int k) -> double * {
-        const int pos = j1 + k * r + 1 + p;   // matrix column (right) or row (left)
-        return left ? X + (size_t)(pos - 1) + (size_t)(ln - 1) * ld : X + (size_t)(ln - 1) + (size_t)(pos - 1) * ld;
-    };
-    auto valid = [=](int ln, int p, int k) -> bool { return ln <= n && p < w && j1 + k * r + 1 + p <= n; };
-
     // U planes of block kbeg
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(P + (size_t)kbeg * kPlaneWords);
-        uint4 *dst = reinterpret_cast<uint4 *>(planes[0]);
-        for (int e = tid; e < kPlaneWords / 2; e += kEmuWarps * 32) cp_async16(dst + e, src + e);
+        uint4 *dst = reinterpret_cast<uint4 *>(S.planes[0]);
+        for (int e = tid; e < kPlaneWords / 2; e += kEmuThreads) cp_async16(dst + e, src + e);
         cp_async_commit();
     }
-
-    long long xv[2][2][2][2];   // [line][kt][h][pair] window values, xv 2^unit[line]
-    double dv[2][2][2];         // [line][h][pair] FP64 values entering at kt = 0
-    int unit[2];
-    // first window: positions of kt = 1 in fixed point at their own scale, kt = 0 as FP64
-    {
-        int em[2] = {kZeroExp, kZeroExp};
-        double v1[2][2][2];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int pr = 0; pr < 2; ++pr) {
-                    const int ln = rr ? lineB : lineA;
-                    const int p = 8 * h + 2 * c + pr;
-                    dv[rr][h][pr] = valid(ln, p, kbeg) ? *addr(ln, p, kbeg) : 0.0;
-                    v1[rr][h][pr] = valid(ln, p + 16, kbeg) ? *addr(ln, p + 16, kbeg) : 0.0;
-                    em[rr] = imax(em[rr], exp_of_f64(v1[rr][h][pr]));
-                }
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            em[rr] = imax(em[rr], __shfl_xor_sync(0xffffffffu, em[rr], 1));
-            em[rr] = imax(em[rr], __shfl_xor_sync(0xffffffffu, em[rr], 2));
-            unit[rr] = (em[rr] == kZeroExp ? 0 : em[rr] + 2) - 64;
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int pr = 0; pr < 2; ++pr) {
-                    xv[rr][1][h][pr] = f64_to_fixed(v1[rr][h][pr], unit[rr]);
-                    xv[rr][0][h][pr] = 0;
-                }
-        }
-    }
-
-    for (int k = kbeg; k >= kend; --k) {
-        const bool last = (k == kend);
-        const int buf = (kbeg - k) & 1;
-        // next block's planes
-        if (!last) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(P + (size_t)(k - 1) * kPlaneWords);
-            uint4 *dst = reinterpret_cast<uint4 *>(planes[buf ^ 1]);
-            for (int e = tid; e < kPlaneWords / 2; e += kEmuWarps * 32) cp_async16(dst + e, src + e);
-        }
-        cp_async_commit();
-
-        // ---- scale of each line: the largest entry of its window
-        int ua[2];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            int em = kZeroExp;
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int pr = 0; pr < 2; ++pr) {
-                    em = imax(em, exp_of_f64(dv[rr][h][pr]));
-                    em = imax(em, exp_of_fixed(xv[rr][1][h][pr], unit[rr]));
-                }
-            em = imax(em, __shfl_xor_sync(0xffffffffu, em, 1));
-            em = imax(em, __shfl_xor_sync(0xffffffffu, em, 2));
-            ua[rr] = (em == kZeroExp ? 0 : em + 2) - 64;   // |x| < 2^62
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int pr = 0; pr < 2; ++pr) {
-                    xv[rr][0][h][pr] = f64_to_fixed(dv[rr][h][pr], ua[rr]);
-                    xv[rr][1][h][pr] = refix(xv[rr][1][h][pr], unit[rr], ua[rr]);
-                }
-        }
-
-        // ---- new columns of the next window (positions 0 .. r-1)
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int pr = 0; pr < 2; ++pr) {
-                    const int ln = rr ? lineB : lineA;
-                    const int p = 8 * h + 2 * c + pr;
-                    dv[rr][h][pr] = (!last && valid(ln, p, k - 1)) ? *addr(ln, p, k - 1) : 0.0;
-                }
-
-        // ---- A operands: digits of the window
-        unsigned af[kDigits][2][4];
-#pragma unroll
-        for (int kt = 0; kt < 2; ++kt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int rr = 0; rr < 2; ++rr) {
-                    unsigned d0[kDigits], d1[kDigits];
-                    digits_bf16(xv[rr][kt][h][0], d0);
-                    digits_bf16(xv[rr][kt][h][1], d1);
-#pragma unroll
-                    for (int t = 0; t < kDigits; ++t) af[t][kt][2 * h + rr] = pack_bf16(d0[t], d1[t]);
-                }
-
-        // ---- line activity (left updates: columns right of the cut of block k)
-        bool act0 = true, act1 = true;
-        if (left) {
-            const int cut = (kind == 5) ? imin(jl + (k + 1) * r, n) : jl + imax(0, (k - 1) * r + 1);
-            act0 = lineA > cut;
-            act1 = lineB > cut;
-        }
-
-        cp_async_wait<1>();
-        __syncthreads();
-        const uint2 *pl = planes[buf];
-
-        // ---- products, one n-tile (8 output positions) at a time; results replace xv
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            float acc[kTopLevel - 1][4];
-#pragma unroll
-            for (int d = 0; d < kTopLevel - 1; ++d)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[d][e] = 0.0f;
-#pragma unroll
-            for (int t = 0; t < kDigits; ++t) {
-                const uint2 b0 = pl[((t * 2 + 0) * 4 + nt) * 32 + lane];
-                const uint2 b1 = pl[((t * 2 + 1) * 4 + nt) * 32 + lane];
-#pragma unroll
-                for (int i = 0; i < kDigits; ++i) {
-                    if (i + t + 2 <= kTopLevel) {   // level (i+1) + (t+1)
-                        mma_bf16(acc[i + t], af[i][0], b0.x, b0.y);
-                        mma_bf16(acc[i + t], af[i][1], b1.x, b1.y);
-                    }
-                }
-            }
-            // levels 2..9 -> one integer in units 2^(ua + 3): level L weighs 2^(8 (8 - L))
-            const int kt = nt >> 1, h = nt & 1;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int c2 = f32_exact_int(acc[0][e]), c3 = f32_exact_int(acc[1][e]);
-                const int c4 = f32_exact_int(acc[2][e]), c5 = f32_exact_int(acc[3][e]);
-                const int c6 = f32_exact_int(acc[4][e]), c7 = f32_exact_int(acc[5][e]);
-                const int c8 = f32_exact_int(acc[6][e]), c9 = f32_exact_int(acc[7][e]);
-                const int lo = (c7 << 8) + c8 + ((c9 + 128) >> 8);
-                const int mid = (c5 << 8) + c6;
-                const long long hi = ((long long)c2 << 16) + (long long)((c3 << 8) + c4);
-                const long long val = (hi << 32) + ((long long)mid << 16) + (long long)lo;
-                const int rr = e >> 1, pr = e & 1;
-                const bool act = rr ? act1 : act0;
-                xv[rr][kt][h][pr] = act ? val : refix(xv[rr][kt][h][pr], ua[rr], ua[rr] + 3);
-            }
-        }
-        __syncthreads();   // planes[buf] is refilled by the next iteration's copy
-
-        // ---- finished positions leave the window (all positions after the last block)
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const int ln = rr ? lineB : lineA;
-            unit[rr] = ua[rr] + 3;
-#pragma unroll
-            for (int kt = 0; kt < 2; ++kt)
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int pr = 0; pr < 2; ++pr) {
-                        const int p = 16 * kt + 8 * h + 2 * c + pr;
-                        if ((last || p >= w - r) && valid(ln, p, k))
-                            *addr(ln, p, k) = fixed_to_f64(xv[rr][kt][h][pr], unit[rr]);
-                    }
-            // slide: positions p < w - r move to p + r (kt 0 -> 1)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int pr = 0; pr < 2; ++pr) {
-                    const int p = 8 * h + 2 * c + pr;
-                    xv[rr][1][h][pr] = (p < w - r) ? xv[rr][0][h][pr] : 0;
-                }
-        }
-    }
+    if (warp & 1) emu_worker<1>(a, S, kind, X, ld, P, l0, kbeg, kend);
+    else emu_worker<0>(a, S, kind, X, ld, P, l0, kbeg, kend);
     cp_async_wait<0>();
 }
 
@@ -451,8 +499,11 @@ cudaError_t launch_s2_form_u(const FormUArgs &a, cudaStream_t st)
 cudaError_t launch_s2_emu_apply(const EmuArgs &a, int nmat, cudaStream_t st)
 {
     if (nmat <= 0) return cudaSuccess;
+    const int sm = (int)sizeof(EmuSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_s2_emu_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
     dim3 grid((a.n + kEmuRows - 1) / kEmuRows, nmat);
-    k_s2_emu_apply<<<grid, kEmuWarps * 32, 0, st>>>(a);
+    k_s2_emu_apply<<<grid, kEmuThreads, sm, st>>>(a);
     return cudaGetLastError();
 }
 
