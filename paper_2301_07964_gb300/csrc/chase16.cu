@@ -122,18 +122,71 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// The left reflectors of block kk of sweeps j1 .. j1+ns-1, their taus and Gram entries into
+// shared memory (threads t0, t0 + nt, ...).  Reflectors that do not exist read as zero.
+__device__ __forceinline__ void load_lazy(const GenArgs &a, int kk, int ns, double *lv, double *lt, double *gr, int t0,
+                                          int nt)
+{
+    const int n = a.n, r = a.r, j1 = a.j1, kdim = a.R.kdim, qm = a.qmax;
+    for (int e = t0; e < ns * r; e += nt) {
+        const int sh = e / r, i = e % r;
+        lv[sh * kLD + i] = (kk < nblocks_gen(n, r, j1 + sh)) ? __ldcg(a.R.VQ + ((size_t)sh * kdim + kk) * r + i) : 0.0;
+    }
+    for (int e = t0; e < ns; e += nt)
+        lt[e] = (kk < nblocks_gen(n, r, j1 + e)) ? __ldcg(a.R.TQ + (size_t)e * kdim + kk) : 0.0;
+    for (int e = t0; e < ns * ns; e += nt) {
+        const int ra = e / ns, rb = e % ns;
+        gr[ra * kM + rb] = (ra < rb && kk < nblocks_gen(n, r, j1 + rb))
+                               ? __ldcg(a.gram + ((size_t)kk * qm + ra) * qm + rb) : 0.0;
+    }
+}
+
+// Bulk part of one RQ step: the rows of W above the next pivot row and all rows of G, three
+// lanes per row, E elements per lane (E = ceil((piv + 1) / 3) covers the live columns).
+template <int E>
+__device__ __forceinline__ void rq_bulk(double *W, double *G, const double *hu, double s1, double sc2, int piv, int m,
+                                        int bw, int lane)
+{
+    const int nrows = (piv - 1) + m;
+    const int rho = bw * 10 + lane / 3, sub = lane % 3;
+    const bool own = lane < 30 && rho < nrows;
+    double *rowp = (rho < piv - 1) ? &W[rho * kLD] : &G[(rho - (piv - 1)) * kLD];
+    double yv[E], uv[E];
+    double p = 0.0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int cc = sub + 3 * e;
+        const bool in = own && cc <= piv;
+        yv[e] = in ? rowp[cc] : 0.0;
+        uv[e] = in ? hu[cc] : 0.0;
+        p = fma(yv[e], uv[e], p);
+    }
+    const int base = lane - sub;
+    const double p1 = __shfl_sync(kFull, p, (base + 1) & 31);
+    const double p2 = __shfl_sync(kFull, p, (base + 2) & 31);
+    const double p0 = __shfl_sync(kFull, p, base & 31);
+    const double cf = (p0 + p1 + p2) * sc2;
+    if (own) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int cc = sub + 3 * e;
+            if (cc <= piv) rowp[cc] = fma(-cf, uv[e], s1 * yv[e]);
+        }
+    }
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(kGenThreads) k_s2_chase16(GenArgs a)
+__global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
 {
     __shared__ double col[2 * kMaxR];      // pivot column segment
     __shared__ double bcol[2 * kMaxR];     // newest B column segment
     __shared__ double W[kM * kLD];         // B block (row-major), then the RQ work array
     __shared__ double Wq[kM * kLD];        // B block after Q^ (band rows i1 .. i2 of B)
     __shared__ double G[kM * kLD];         // accumulated right factor of the RQ (row-major)
-    __shared__ double lv[kM * kLD];        // earlier sweeps' left reflectors of block k
-    __shared__ double lt[kM];
-    __shared__ double gr[kM * kM];         // their Gram entries tau_b u_a.u_b, a < b
+    __shared__ double lvb[2][kM * kLD];    // earlier sweeps' left reflectors of block k (buffer k & 1)
+    __shared__ double ltb[2][kM];
+    __shared__ double grb[2][kM * kM];     // their Gram entries tau_b u_a.u_b, a < b
     __shared__ double hu[2][kM];           // RQ reflector vectors (double buffered)
     __shared__ double hs[2][2];            // RQ scale factors {s1, sc2}; s1 = 0: identity
     __shared__ double pu[kM];              // current Q^ / Z^ vector
@@ -247,17 +300,8 @@ __global__ void __launch_bounds__(kGenThreads) k_s2_chase16(GenArgs a)
             col[i] = __ldcg(A + AT(lda, rlo + i, g.jb));
             if (hasb) bcol[i] = __ldcg(B + AT(ldb, rlo + i, cb));
         }
-        for (int e = tid; e < nlazy * r; e += kGenThreads) {
-            const int sh = e / r, i = e % r;
-            lv[sh * kLD + i] = (k < nblocks_gen(n, r, j1 + sh)) ? __ldcg(a.R.VQ + ((size_t)sh * kdim + k) * r + i) : 0.0;
-        }
-        for (int e = tid; e < nlazy; e += kGenThreads)
-            lt[e] = (k < nblocks_gen(n, r, j1 + e)) ? __ldcg(a.R.TQ + (size_t)e * kdim + k) : 0.0;
-        for (int e = tid; e < nlazy * nlazy; e += kGenThreads) {
-            const int ra = e / nlazy, rb = e % nlazy;
-            gr[ra * kM + rb] = (ra < rb && k < nblocks_gen(n, r, j1 + rb))
-                                   ? __ldcg(a.gram + ((size_t)k * qm + ra) * qm + rb) : 0.0;
-        }
+        double *lv = lvb[k & 1], *lt = ltb[k & 1], *gr = grb[k & 1];
+        if (k == 0) load_lazy(a, 0, nlazy, lv, lt, gr, tid, kGenThreads);
         if (gen) {
             for (int e = tid; e < m * m; e += kGenThreads) {
                 const int i = e % m, cc = e / m;
@@ -279,26 +323,30 @@ __global__ void __launch_bounds__(kGenThreads) k_s2_chase16(GenArgs a)
         if (nlazy > 0 && L > 0 && (warp == 1 || (warp == 2 && hasb))) {
             double *seg = (warp == 1) ? col : bcol;
             const int ns = nlazy;
+            // lanes 2b and 2b+1 form w_b, each over every other entry of reflector b
+            const int lb = lane >> 1, part = lane & 1;
             double wv = 0.0;
-            if (lane < ns) {
-                const int mb = imin(r, n - (j1 + lane + k * r));
-                const double *ub = lv + lane * kLD;
-                const double *xs = seg + lane;
+            if (lb < ns) {
+                const int mb = imin(r, n - (j1 + lb + k * r));
+                const double *ub = lv + lb * kLD;
+                const double *xs = seg + lb;
                 double d0 = 0.0, d1 = 0.0;
-                for (int i = 0; i < mb; i += 2) {
+                for (int i = part; i < mb; i += 4) {
                     d0 = fma(ub[i], xs[i], d0);
-                    if (i + 1 < mb) d1 = fma(ub[i + 1], xs[i + 1], d1);
+                    if (i + 2 < mb) d1 = fma(ub[i + 2], xs[i + 2], d1);
                 }
-                wv = lt[lane] * (d0 + d1);
+                wv = d0 + d1;
             }
+            wv += __shfl_xor_sync(kFull, wv, 1);
+            if (lb < ns) wv *= lt[lb];
             for (int ra = 0; ra + 1 < ns; ++ra) {
-                const double da = __shfl_sync(kFull, wv, ra);
-                if (lane > ra && lane < ns) wv = fma(-da, gr[ra * kM + lane], wv);
+                const double da = __shfl_sync(kFull, wv, 2 * ra);
+                if (lb > ra && lb < ns) wv = fma(-da, gr[ra * kM + lb], wv);
             }
-            // lane b holds d_b; lane i: x_i -= sum_b d_b u_b(i - b)  (L <= 31)
+            // lanes 2b, 2b+1 hold d_b; lane i: x_i -= sum_b d_b u_b(i - b)  (L <= 31)
             double e0 = 0.0, e1 = 0.0;
             for (int rb = 0; rb < ns; ++rb) {
-                const double db = __shfl_sync(kFull, wv, rb);
+                const double db = __shfl_sync(kFull, wv, 2 * rb);
                 const int mb = imin(r, n - (j1 + rb + k * r));
                 const int i0 = lane - rb;
                 const double u = (i0 >= 0 && i0 < mb) ? lv[rb * kLD + i0] : 0.0;
@@ -362,11 +410,15 @@ __global__ void __launch_bounds__(kGenThreads) k_s2_chase16(GenArgs a)
 
         // pivot and B column segments are final (the B column's block rows are rewritten with
         // the band); warp 4 stores them while the RQ runs
-        if (warp == 4)
+        if (warp == 4) {
             for (int i = lane; i < L; i += 32) {
                 A[AT(lda, rlo + i, g.jb)] = col[i];
                 if (hasb) B[AT(ldb, rlo + i, cb)] = bcol[i];
             }
+            // the earlier sweeps' data of block k+1 is final: sweep j-1 has finished block k+2
+            // and its helper block k+1 (the waits of this step)
+            if (k + 1 < kl) load_lazy(a, k + 1, nlazy, lvb[(k + 1) & 1], ltb[(k + 1) & 1], grb[(k + 1) & 1], lane, 32);
+        }
 
         // ---- 4. RQ of the B block with look-ahead (warps 0 .. 3)
         if (gen && m >= 2 && warp < 4) {
@@ -417,34 +469,19 @@ __global__ void __launch_bounds__(kGenThreads) k_s2_chase16(GenArgs a)
                         }
                     }
                 } else {
-                    // bulk: W rows 0 .. piv-2 and G rows 0 .. m-1, three lanes per row
+                    // bulk: W rows 0 .. piv-2 and G rows 0 .. m-1, three lanes per row, only the
+                    // live columns 0 .. piv; a warp without rows skips the step
                     const double bs1 = hs[cur][0];
-                    const int nrows = (piv - 1) + m;
-                    const int rho = (warp - 1) * 10 + lane / 3, sub = lane % 3;
-                    const bool own = lane < 30 && rho < nrows;
-                    if (bs1 != 0.0) {
-                        double *rowp = (rho < piv - 1) ? &W[rho * kLD] : &G[(rho - (piv - 1)) * kLD];
-                        double yv[6], uv[6];
-                        double p = 0.0;
-#pragma unroll
-                        for (int e = 0; e < 6; ++e) {
-                            const int cc = sub + 3 * e;
-                            const bool in = own && cc <= piv;
-                            yv[e] = in ? rowp[cc] : 0.0;
-                            uv[e] = in ? hu[cur][cc] : 0.0;
-                            p = fma(yv[e], uv[e], p);
-                        }
-                        const int base = lane - sub;
-                        const double p1 = __shfl_sync(kFull, p, (base + 1) & 31);
-                        const double p2 = __shfl_sync(kFull, p, (base + 2) & 31);
-                        const double p0 = __shfl_sync(kFull, p, base & 31);
-                        const double cf = (p0 + p1 + p2) * hs[cur][1];
-                        if (own) {
-#pragma unroll
-                            for (int e = 0; e < 6; ++e) {
-                                const int cc = sub + 3 * e;
-                                if (cc <= piv) rowp[cc] = fma(-cf, uv[e], bs1 * yv[e]);
-                            }
+                    const int bw = warp - 1;
+                    if (bs1 != 0.0 && bw * 10 < (piv - 1) + m) {
+                        const double bsc2 = hs[cur][1];
+                        switch ((piv + 3) / 3) {
+                        case 6: rq_bulk<6>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
+                        case 5: rq_bulk<5>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
+                        case 4: rq_bulk<4>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
+                        case 3: rq_bulk<3>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
+                        case 2: rq_bulk<2>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
+                        default: rq_bulk<1>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
                         }
                     }
                 }
