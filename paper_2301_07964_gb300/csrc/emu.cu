@@ -99,9 +99,10 @@ __device__ __forceinline__ long long refix(long long x, int su, int du)
 // ---- balanced digits --------------------------------------------------------------------
 
 // BF16 bit patterns of the 8 balanced base-256 digits of x (|x| < 2^62), most significant
-// first: with u = x + 0x8080808080808080 (no wrap-around in that range), digit i is byte
-// (8 - i) of u minus 128.  A digit in [-128, 127] is formed exactly in FP32 from its byte and
-// its FP32 encoding has 16 trailing zero bits, so the upper half is the exact BF16.
+// first, in the upper halves of FP32 words: with u = x + 0x8080808080808080 (no wrap-around
+// in that range), digit i is byte (8 - i) of u minus 128.  One byte permute places the byte
+// under the exponent of 2^23 and one subtraction removes 2^23 + 128; a digit in [-128, 127]
+// has 16 trailing zero bits in FP32, so the upper half of its encoding is its exact BF16.
 __device__ __forceinline__ void digits_bf16(long long x, unsigned (&bf)[kDigits])
 {
     const unsigned long long u = (unsigned long long)x + 0x8080808080808080ULL;
@@ -109,13 +110,14 @@ __device__ __forceinline__ void digits_bf16(long long x, unsigned (&bf)[kDigits]
 #pragma unroll
     for (int i = 0; i < kDigits; ++i) {
         const unsigned word = (i < 4) ? hi : lo;
-        const unsigned byte = (word >> (8 * (3 - (i & 3)))) & 0xffu;
-        const float f = __uint_as_float(0x4B000000u | byte) - 8388736.0f;   // byte - 128
-        bf[i] = __float_as_uint(f) >> 16;
+        const unsigned sel = 0x7650u | (unsigned)(3 - (i & 3));   // bytes {b, 0, 0, 0x4B}
+        bf[i] = __float_as_uint(__uint_as_float(__byte_perm(word, 0x4B000000u, sel)) - 8388736.0f);
     }
 }
 
-__device__ __forceinline__ unsigned pack_bf16(unsigned lo, unsigned hi) { return lo | (hi << 16); }
+// Two BF16 values (the upper halves of the FP32 words lo and hi) in one register, lo in the
+// low half.
+__device__ __forceinline__ unsigned pack_bf16(unsigned lo, unsigned hi) { return __byte_perm(lo, hi, 0x7632u); }
 
 // An FP32 value holding an integer of magnitude below 2^22, as int (exact).
 __device__ __forceinline__ int f32_exact_int(float c) { return __float_as_int(c + 12582912.0f) - 0x4B400000; }
