@@ -141,6 +141,33 @@ __device__ __forceinline__ void load_lazy(const GenArgs &a, int kk, int ns, doub
     }
 }
 
+// Index ranges of step (k, j) of the main block (see step_geom): pivot column segment
+// rows rlo .. rhi (L of them), newest B column cb, block size m, and the band rows the main
+// block updates: A rows x0 .. i3 (na), B rows x0 .. i1-1 above the block (nbt), then the
+// block rows (nband in all; rows i4 .. cr-1 belong to the helper block).
+struct StepInfo {
+    StepGeom g;
+    bool gen, hasb;
+    int rlo, L, cb, m, x0, na, nbt, nband;
+};
+
+__device__ __forceinline__ StepInfo step_info(int n, int r, int j1, int qg, int kg, int k, int j)
+{
+    StepInfo I;
+    I.g = step_geom(n, r, j1, qg, k, j);
+    I.gen = k < kg;
+    I.rlo = j1 + k * r + 1;
+    I.L = imin(j + (k + 1) * r, n) - I.rlo + 1;
+    I.cb = I.g.i1 + r - 1;
+    I.hasb = I.cb <= n;
+    I.m = I.g.i2 - I.g.i1 + 1;
+    I.x0 = imax(I.g.i4, I.rlo);
+    I.na = I.gen ? imax(0, I.g.i3 - I.x0 + 1) : 0;
+    I.nbt = I.gen ? I.g.i1 - I.x0 : 0;
+    I.nband = I.gen ? I.na + I.nbt + I.m : 0;
+    return I;
+}
+
 // Bulk part of one RQ step: the rows of W above the next pivot row and all rows of G, three
 // lanes per row, E elements per lane (E = ceil((piv + 1) / 3) covers the live columns).
 template <int E>
@@ -268,56 +295,68 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
     const int c = lane & 15;   // panel lanes: column index (both half-warps hold the same data)
     double brow[kM];           // band threads: their row
 
-    for (int k = 0; k < kl; ++k) {
-        // ---- wait until sweep j-1 has finished block k+2 (or all of its blocks), and its helper
-        //      block k+1 (its rows of block k+1 hold the upper rows of this step's B column)
-        if (tid == 128 && s > 0)
-            s_abort = !(wait_at_least(a.flags + s - 1, a.epoch | (unsigned long long)imin(k + 3, kl_prev), a.status,
-                                      a.group, k, j) &&
-                        wait_at_least(hflags + s - 1, a.epoch | (unsigned long long)(k + 2), a.status, a.group, k, j));
-        __syncthreads();
-        if (s_abort) return;
-
-        const StepGeom g = step_geom(n, r, j1, qg, k, j);
-        const bool gen = k < kg;
-        const int rlo = j1 + k * r + 1;
-        const int rhi = imin(j + (k + 1) * r, n);
-        const int L = rhi - rlo + 1;
-        const int cb = g.i1 + r - 1;
-        const bool hasb = cb <= n;
-        const int m = g.i2 - g.i1 + 1;
-        const int off = j - j1;
-        // band rows of the main block (rows >= cr = rlo; the helper takes i4 .. cr-1):
-        // A rows x0 .. i3, B rows x0 .. i1-1 above the block, then the block rows i1 .. i2
-        const int x0 = imax(g.i4, rlo);
-        const int na = gen ? imax(0, g.i3 - x0 + 1) : 0;
-        const int nbt = gen ? g.i1 - x0 : 0;
-        const int nband = gen ? na + nbt + m : 0;
-        const int bt = tid - 160;   // band thread index (warps 5 .. 7)
-
-        // ---- 1. prefetch
-        for (int i = tid; i < L; i += kGenThreads) {
-            col[i] = __ldcg(A + AT(lda, rlo + i, g.jb));
-            if (hasb) bcol[i] = __ldcg(B + AT(ldb, rlo + i, cb));
+    const int bt = tid - 160;   // band thread index (warps 5 .. 7)
+    // Global loads of a step's pivot column segment, B column, B block and band rows, into
+    // registers (the band rows straight into brow); committed to shared memory later.
+    double pc = 0.0, pb = 0.0, pw = 0.0;
+    auto issue_loads = [&](const StepInfo &I) {
+        if (tid < I.L) {
+            pc = __ldcg(A + AT(lda, I.rlo + tid, I.g.jb));
+            if (I.hasb) pb = __ldcg(B + AT(ldb, I.rlo + tid, I.cb));
         }
-        double *lv = lvb[k & 1], *lt = ltb[k & 1], *gr = grb[k & 1];
-        if (k == 0) load_lazy(a, 0, nlazy, lv, lt, gr, tid, kGenThreads);
-        if (gen) {
-            for (int e = tid; e < m * m; e += kGenThreads) {
-                const int i = e % m, cc = e / m;
-                if (!(hasb && cc == m - 1)) W[i * kLD + cc] = __ldcg(B + AT(ldb, g.i1 + i, g.i1 + cc));
-                G[i * kLD + cc] = (i == cc) ? 1.0 : 0.0;
-            }
+        if (I.gen && tid < I.m * I.m) {
+            const int i = tid % I.m, cc = tid / I.m;
+            if (!(I.hasb && cc == I.m - 1)) pw = __ldcg(B + AT(ldb, I.g.i1 + i, I.g.i1 + cc));
         }
-        if (bt >= 0 && bt < na + nbt) {
-            const bool isA = bt < na;
-            const int x = x0 + (isA ? bt : bt - na);
-            const double *src = isA ? A + AT(lda, x, g.i1) : B + AT(ldb, x, g.i1);
+        if (bt >= 0 && bt < I.na + I.nbt) {
+            const bool isA = bt < I.na;
+            const int x = I.x0 + (isA ? bt : bt - I.na);
+            const double *src = isA ? A + AT(lda, x, I.g.i1) : B + AT(ldb, x, I.g.i1);
             const size_t ld = isA ? (size_t)lda : (size_t)ldb;
 #pragma unroll
-            for (int cc = 0; cc < kM; ++cc) brow[cc] = (cc < m) ? __ldcg(src + cc * ld) : 0.0;
+            for (int cc = 0; cc < kM; ++cc) brow[cc] = (cc < I.m) ? __ldcg(src + cc * ld) : 0.0;
         }
-        __syncthreads();
+    };
+    auto commit_loads = [&](const StepInfo &I) {
+        if (tid < I.L) {
+            col[tid] = pc;
+            if (I.hasb) bcol[tid] = pb;
+        }
+        if (I.gen && tid < I.m * I.m) {
+            const int i = tid % I.m, cc = tid / I.m;
+            if (!(I.hasb && cc == I.m - 1)) W[i * kLD + cc] = pw;
+            G[i * kLD + cc] = (i == cc) ? 1.0 : 0.0;
+        }
+    };
+    // step k waits until sweep j-1 has finished block k+2 (or all of its blocks) and its helper
+    // block k+1 (whose rows of block k+1 hold the upper rows of step k's B column)
+    auto wait_deps = [&](int k) -> bool {
+        return wait_at_least(a.flags + s - 1, a.epoch | (unsigned long long)imin(k + 3, kl_prev), a.status, a.group,
+                             k, j) &&
+               wait_at_least(hflags + s - 1, a.epoch | (unsigned long long)(k + 2), a.status, a.group, k, j);
+    };
+
+    // step 0's dependencies and data
+    if (tid == 128 && s > 0) s_abort = !wait_deps(0);
+    __syncthreads();
+    if (s_abort) return;
+    StepInfo I = step_info(n, r, j1, qg, kg, 0, j);
+    issue_loads(I);
+    commit_loads(I);
+    load_lazy(a, 0, nlazy, lvb[0], ltb[0], grb[0], tid, kGenThreads);
+    __syncthreads();
+
+    for (int k = 0; k < kl; ++k) {
+        const StepGeom g = I.g;
+        const bool gen = I.gen;
+        const int rlo = I.rlo;
+        const int L = I.L;
+        const int cb = I.cb;
+        const bool hasb = I.hasb;
+        const int m = I.m;
+        const int off = j - j1;
+        const int x0 = I.x0, na = I.na, nbt = I.nbt, nband = I.nband;
+        double *lv = lvb[k & 1], *lt = ltb[k & 1], *gr = grb[k & 1];
 
         // ---- 2. lazy left updates (warp 1: pivot column, warp 2: B column)
         if (nlazy > 0 && L > 0 && (warp == 1 || (warp == 2 && hasb))) {
@@ -490,6 +529,9 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
         }
         __syncthreads();
 
+        // warp 4 takes the next step's dependencies while Z^ and the band update run
+        if (tid == 128 && s > 0 && k + 1 < kl) s_abort = !wait_deps(k + 1);
+
         if (gen) {
             // ---- 5. opposite reflector Z^ from G(:, 1) (panel); band dots (warps 5 .. 7)
             double p = 0.0;
@@ -547,11 +589,26 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
             }
         }
 
-        // ---- 6. publish block k of this sweep
+        // ---- 6. publish block k of this sweep; the next step's global loads (its dependencies
+        //      were acquired by warp 4 above, and this step's band stores are ordered before
+        //      them by the barrier) are in flight while the stores of this step are fenced
+        __syncthreads();
+        const bool more = k + 1 < kl && !s_abort;
+        StepInfo In = I;
+        if (more) {
+            In = step_info(n, r, j1, qg, kg, k + 1, j);
+            issue_loads(In);
+        }
         __threadfence();
         __syncthreads();
         if (tid == 0 && !(a.stall && s == 0))
             st_release_u64(a.flags + s, a.epoch | (unsigned long long)(k + 1));
+        if (s_abort) return;
+        if (more) {
+            commit_loads(In);
+            I = In;
+            __syncthreads();
+        }
     }
 }
 
