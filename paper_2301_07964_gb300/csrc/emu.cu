@@ -22,7 +22,7 @@
 // the largest entry of each row window; U_k (orthogonal, entries in [-1, 1]) uses the fixed
 // scale 2^-61.  No FP64 instruction runs in the update loop: FP64 values enter and leave
 // through integer bit manipulation of their IEEE-754 encoding.
-#include "hts_internal.cuh"
+#include "right_window.cuh"
 
 namespace hts {
 
@@ -453,11 +453,16 @@ __global__ void __launch_bounds__(kEmuThreads) k_s2_emu_apply(EmuArgs a)
     const int l0 = tile * kEmuRows + 1;
     const int llast = imin(l0 + kEmuRows - 1, n);
     int kbeg = kmax, kend = 0;
+    int skstart = -1, skstop = 0;   // staircase blocks (rows of A and B)
     if (kind <= 1) {
         // rows of A and B: blocks whose whole reflector set is still pending for every row
-        // of the tile (the rest, the staircase, is left to the FP64 kernel)
+        // of the tile are emulated; the blocks below them down to the last one any row of the
+        // tile needs (x < i4(k, j1+qg-1) = j1 + 1 + max(0, (k-1) r)) form the staircase,
+        // applied reflector by reflector in native FP64 afterwards
         const int kT = (llast <= j1) ? -1 : qg + (llast - j1 - 1) / r;
         kend = kT + 1;
+        skstart = imin(kT, kmax);
+        skstop = (l0 <= j1) ? 0 : (l0 - j1 - 1) / r + 2;
     } else if (left) {
         const int isB = kind == 5;
         kbeg = -1;
@@ -466,18 +471,25 @@ __global__ void __launch_bounds__(kEmuThreads) k_s2_emu_apply(EmuArgs a)
             if (cut < llast) { kbeg = k; break; }
         }
     }
-    if (kbeg < kend || l0 > n) return;
+    if (l0 > n) return;
 
-    // U planes of block kbeg
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(P + (size_t)kbeg * kPlaneWords);
-        uint4 *dst = reinterpret_cast<uint4 *>(S.planes[0]);
-        for (int e = tid; e < kPlaneWords / 2; e += kEmuThreads) cp_async16(dst + e, src + e);
-        cp_async_commit();
+    if (kbeg >= kend) {
+        // U planes of block kbeg
+        {
+            const uint4 *src = reinterpret_cast<const uint4 *>(P + (size_t)kbeg * kPlaneWords);
+            uint4 *dst = reinterpret_cast<uint4 *>(S.planes[0]);
+            for (int e = tid; e < kPlaneWords / 2; e += kEmuThreads) cp_async16(dst + e, src + e);
+            cp_async_commit();
+        }
+        if (warp & 1) emu_worker<1>(a, S, kind, X, ld, P, l0, kbeg, kend);
+        else emu_worker<0>(a, S, kind, X, ld, P, l0, kbeg, kend);
+        cp_async_wait<0>();
     }
-    if (warp & 1) emu_worker<1>(a, S, kind, X, ld, P, l0, kbeg, kend);
-    else emu_worker<0>(a, S, kind, X, ld, P, l0, kbeg, kend);
-    cp_async_wait<0>();
+    if (kind <= 1 && skstop <= skstart) {
+        __syncthreads();   // the tile's emulated results are stored; shared memory is reused
+        right_window_rows<kEmuThreads>(X, (int)ld, kind, a.R.VZ, a.R.TZ, a.R.kdim, n, r, j1, qg, l0, skstart,
+                                       skstop, reinterpret_cast<double *>(emu_smem));
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -486,8 +498,6 @@ __global__ void __launch_bounds__(kEmuThreads) k_s2_emu_apply(EmuArgs a)
 size_t emu_plane_bytes(int kdim) { return (size_t)kdim * kPlaneWords * sizeof(uint2); }
 
 bool emu_supported(int r, int qg) { return r == 16 && qg >= 1 && r + qg - 1 <= 32; }
-
-int emu_tile_rows() { return kEmuRows; }
 
 cudaError_t launch_s2_form_u(const FormUArgs &a, cudaStream_t st)
 {

@@ -127,7 +127,7 @@ GroupCost s2_group_cost(int n, int r, int j1, int qg, bool hasQ, bool hasZ, bool
     GroupCost c{};
     const int jl = j1 + qg - 1;
     const int kmax = nblocks_gen(n, r, j1) - 1;
-    const int er = emu_tile_rows();
+    const int er = 64;   // rows per tile of the emulated right update
     for (int j = j1; j <= jl; ++j) {
         const int kg = nblocks_gen(n, r, j);
         for (int k = 0; k < kg; ++k) {
@@ -271,25 +271,22 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
             ea.M[1] = B; ea.ld[1] = ldb; ea.kind[1] = 1;
             for (int i = 2; i < 4; ++i) { ea.M[i] = nullptr; ea.ld[i] = 1; ea.kind[i] = 0; }
             ea.n = n; ea.r = r; ea.j1 = j1; ea.qg = qg;
-            ea.planesQ = PQ[set]; ea.planesZ = PZ[set]; ea.status = ctx->d_status;
+            ea.planesQ = PQ[set]; ea.planesZ = PZ[set]; ea.R = R[set]; ea.status = ctx->d_status;
             {
+                // emulated blocks and, per tile, the staircase blocks in native FP64
                 ProfScope ps(ctx, st);
                 if ((e = launch_s2_emu_apply(ea, 2, st)) != cudaSuccess) return HTS_ERR_CUDA;
-                ps.done(HTS_K_EMU_RIGHT, gc.f_right, gc.b_right, gc.m_right);
+                ps.done(HTS_K_EMU_RIGHT, gc.f_right + gc.f_stair, gc.b_right + gc.b_stair, gc.m_right);
             }
-        }
-
-        ApplyArgs aa;
-        aa.M[0] = A; aa.ld[0] = lda; aa.kind[0] = 0;
-        aa.M[1] = B; aa.ld[1] = ldb; aa.kind[1] = 1;
-        for (int i = 2; i < 4; ++i) { aa.M[i] = nullptr; aa.ld[i] = 1; aa.kind[i] = 0; }
-        aa.n = n; aa.r = r; aa.j1 = j1; aa.qg = qg; aa.R = R[set]; aa.status = ctx->d_status;
-        aa.emu_rows = emu ? emu_tile_rows() : 0;
-        {
+        } else {
+            ApplyArgs aa;
+            aa.M[0] = A; aa.ld[0] = lda; aa.kind[0] = 0;
+            aa.M[1] = B; aa.ld[1] = ldb; aa.kind[1] = 1;
+            for (int i = 2; i < 4; ++i) { aa.M[i] = nullptr; aa.ld[i] = 1; aa.kind[i] = 0; }
+            aa.n = n; aa.r = r; aa.j1 = j1; aa.qg = qg; aa.R = R[set]; aa.status = ctx->d_status;
             ProfScope ps(ctx, st);
             if ((e = launch_s2_apply_right(aa, 2, st)) != cudaSuccess) return HTS_ERR_CUDA;
-            if (emu) ps.done(HTS_K_APPLY_RIGHT, gc.f_stair, gc.b_stair);
-            else ps.done(HTS_K_APPLY_RIGHT, gc.f_right, gc.b_right);
+            ps.done(HTS_K_APPLY_RIGHT, gc.f_right, gc.b_right);
         }
 
         if (emu) {
@@ -298,7 +295,7 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
             el.M[1] = B; el.ld[1] = ldb; el.kind[1] = 5;
             for (int i = 2; i < 4; ++i) { el.M[i] = nullptr; el.ld[i] = 1; el.kind[i] = 0; }
             el.n = n; el.r = r; el.j1 = j1; el.qg = qg;
-            el.planesQ = PQ[set]; el.planesZ = PZ[set]; el.status = ctx->d_status;
+            el.planesQ = PQ[set]; el.planesZ = PZ[set]; el.R = R[set]; el.status = ctx->d_status;
             ProfScope ps(ctx, st);
             if ((e = launch_s2_emu_apply(el, 2, st)) != cudaSuccess) return HTS_ERR_CUDA;
             ps.done(HTS_K_EMU_LEFT, gc.f_left, gc.b_left, gc.m_left);
@@ -322,7 +319,7 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
                 if (Q) { eq.M[nq] = Q; eq.ld[nq] = ldq; eq.kind[nq] = 3; ++nq; }
                 for (int i = nq; i < 4; ++i) { eq.M[i] = nullptr; eq.ld[i] = 1; eq.kind[i] = 0; }
                 eq.n = n; eq.r = r; eq.j1 = j1; eq.qg = qg;
-                eq.planesQ = PQ[set]; eq.planesZ = PZ[set]; eq.status = ctx->d_status;
+                eq.planesQ = PQ[set]; eq.planesZ = PZ[set]; eq.R = R[set]; eq.status = ctx->d_status;
                 ProfScope ps(ctx, side);
                 if ((e = launch_s2_emu_apply(eq, nq, side)) != cudaSuccess) return HTS_ERR_CUDA;
                 ps.done(HTS_K_EMU_QZ, gc.f_qz, gc.b_qz, gc.m_qz);
@@ -333,7 +330,6 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
                 if (Q) { aq.M[nq] = Q; aq.ld[nq] = ldq; aq.kind[nq] = 3; ++nq; }
                 for (int i = nq; i < 4; ++i) { aq.M[i] = nullptr; aq.ld[i] = 1; aq.kind[i] = 0; }
                 aq.n = n; aq.r = r; aq.j1 = j1; aq.qg = qg; aq.R = R[set]; aq.status = ctx->d_status;
-                aq.emu_rows = 0;
                 ProfScope ps(ctx, side);
                 if ((e = launch_s2_apply_right(aq, nq, side)) != cudaSuccess) return HTS_ERR_CUDA;
                 ps.done(HTS_K_APPLY_QZ, gc.f_qz, gc.b_qz);

@@ -193,9 +193,7 @@ struct GenArgs {
 };
 
 // kind 0 = A, 1 = B (Z^ reflectors on rows x < i4(k, j)), 2 = Z (Z^, all rows),
-// 3 = Q (Q^, all rows).  emu_rows > 0: the blocks of A and B rows that the emulated kernel
-// took (every block whose whole reflector set is pending for all rows of its tile of emu_rows
-// rows) are skipped here.
+// 3 = Q (Q^, all rows)
 struct ApplyArgs {
     double *M[4];
     int ld[4];
@@ -203,7 +201,6 @@ struct ApplyArgs {
     int n, r, j1, qg;
     ReflectorSet R;
     const int *status;
-    int emu_rows;
 };
 
 // Block formation (emu.cu): the products U^Q_k, U^Z_k of a group's reflectors per block k,
@@ -215,14 +212,16 @@ struct FormUArgs {
     const int *status;
 };
 
-// Emulated delayed updates (emu.cu).  kind 0 = A rows, 1 = B rows (blocks above the
-// staircase), 2 = Z rows, 3 = Q rows, 4 = A columns, 5 = B columns (left updates).
+// Emulated delayed updates (emu.cu).  kind 0 = A rows, 1 = B rows (the staircase blocks of
+// each tile in native FP64 from the reflectors in R), 2 = Z rows, 3 = Q rows, 4 = A columns,
+// 5 = B columns (left updates).
 struct EmuArgs {
     double *M[4];
     int ld[4];
     int kind[4];
     int n, r, j1, qg;
     const uint2 *planesQ, *planesZ;
+    ReflectorSet R;
     const int *status;
 };
 
@@ -241,7 +240,6 @@ cudaError_t launch_s2_form_u(const FormUArgs &a, cudaStream_t st);
 cudaError_t launch_s2_emu_apply(const EmuArgs &a, int nmat, cudaStream_t st);
 size_t emu_plane_bytes(int kdim);
 bool emu_supported(int r, int qg);
-int emu_tile_rows();
 cudaError_t launch_s2_apply_right(const ApplyArgs &a, int nmat, cudaStream_t st);
 cudaError_t launch_s2_apply_left(const LeftArgs &a, cudaStream_t st);
 cudaError_t launch_set_identity(double *M, int ld, int n, cudaStream_t st);

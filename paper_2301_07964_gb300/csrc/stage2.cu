@@ -11,7 +11,7 @@
 // The delayed updates walk the blocks k from the last to the first with a sliding window of
 // r + qg - 1 columns (rows), so every element is read and written once per group; inside
 // the window the group's reflectors are applied one at a time in FP64.
-#include "hts_internal.cuh"
+#include "right_window.cuh"
 
 namespace hts {
 
@@ -20,120 +20,27 @@ namespace hts {
 // matrix.  kind 0 = A, 1 = B (Z^ reflectors, rows x < i4(k, j) only: the generate phase
 // updated the rest), 2 = Z (Z^ reflectors, all rows), 3 = Q (Q^ reflectors, all rows).
 // ---------------------------------------------------------------------------------------
-// Four lanes share a row: lane l of the group owns entries l, l+4, ... of each reflector, so a
-// row's chain of dependent operations is a quarter as long as with one thread per row.  The
-// next window's new columns are loaded into registers while the current window is updated.
-constexpr int kRightLanes = 4;
 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_s2_apply_right(ApplyArgs a)
 {
     extern __shared__ double sm[];
     constexpr int NR = NT / kRightLanes;                    // rows per thread block
-    constexpr int kPrefetch = kMaxR * NR / NT;              // new elements per thread
-    const int LDS = NR + 1;
     const int n = a.n, r = a.r, j1 = a.j1, qg = a.qg;
-    const int w = r + qg - 1;
-    double *buf = sm;                       // [w][LDS]: row rr of the tile, window column p
-    double *vr = buf + (size_t)w * LDS;     // [qg][r]
-    double *tr = vr + (size_t)qg * r;       // [qg]
     const int mi = blockIdx.y;
     const int kind = a.kind[mi];
-    double *X = a.M[mi];
-    const int ld = a.ld[mi];
-    const int tid = threadIdx.x;
-    const int rr = tid / kRightLanes, sub = tid % kRightLanes;
     const int x0 = blockIdx.x * NR + 1;
-    const int x = x0 + rr;
     const int kmax = nblocks_gen(n, r, j1) - 1;
-    const int kdim = a.R.kdim;
-    const double *Vs = (kind == 3) ? a.R.VQ : a.R.VZ;
-    const double *Ts = (kind == 3) ? a.R.TQ : a.R.TZ;
 
     if (__ldcg(a.status) != 0) return;
-    int kstop = 0, kstart = kmax;
+    int kstop = 0;
     if (kind <= 1) {
         // rows x0.. need block k only while x0 < i4(k, j1+qg-1) = j1 + 1 + max(0, (k-1) r)
         kstop = (x0 <= j1) ? 0 : (x0 - j1 - 1) / r + 2;
-        if (a.emu_rows > 0) {
-            // the emulated kernel applied blocks k > kT of this row tile
-            const int xt = imin(((x0 - 1) / a.emu_rows + 1) * a.emu_rows, n);
-            const int kT = (xt <= j1) ? -1 : qg + (xt - j1 - 1) / r;
-            kstart = imin(kstart, kT);
-        }
-        if (kstop > kstart) return;
+        if (kstop > kmax) return;
     }
-
-    // window kstart: all w columns
-    {
-        const int c0 = j1 + kstart * r + 1;
-        for (int e = tid; e < w * NR; e += NT) {
-            const int p = e / NR, re = e % NR;
-            const int c = c0 + p, xr = x0 + re;
-            if (c <= n && xr <= n) buf[p * LDS + re] = X[AT(ld, xr, c)];
-        }
-    }
-    double pre[kPrefetch];
-    for (int k = kstart; k >= kstop; --k) {
-        const int c0 = j1 + k * r + 1;
-        for (int e = tid; e < qg * r; e += NT) {
-            const int sidx = e / r, i = e % r;
-            vr[e] = Vs[((size_t)sidx * kdim + k) * r + i];
-        }
-        for (int e = tid; e < qg; e += NT) tr[e] = Ts[(size_t)e * kdim + k];
-        // prefetch the r new columns of window k-1 (columns c0-r .. c0-1)
-        if (k > kstop) {
-#pragma unroll
-            for (int t = 0; t < kPrefetch; ++t) {
-                const int e = tid + t * NT;
-                const int p = e / NR, re = e % NR;
-                const int c = c0 - r + p, xr = x0 + re;
-                pre[t] = (p < r && xr <= n) ? X[AT(ld, xr, c)] : 0.0;
-            }
-        }
-        __syncthreads();
-        for (int sidx = 0; sidx < qg; ++sidx) {
-            const double tau = tr[sidx];
-            if (tau == 0.0) continue;
-            const int jj = j1 + sidx;
-            const bool active = x <= n && (kind > 1 || x < j1 + 1 + imax(0, (k + jj - j1 - qg) * r));
-            const int mlen = imin(r, n - (jj + k * r));
-            const double *v = vr + sidx * r;
-            double *b = buf + sidx * LDS + rr;
-            double d = 0.0;
-            if (active)
-                for (int i = sub; i < mlen; i += kRightLanes) d += b[i * LDS] * v[i];
-            d += __shfl_xor_sync(0xffffffffu, d, 1);
-            d += __shfl_xor_sync(0xffffffffu, d, 2);
-            d *= tau;
-            if (active)
-                for (int i = sub; i < mlen; i += kRightLanes) b[i * LDS] -= d * v[i];
-        }
-        __syncthreads();
-        // store the columns that leave the window, keep the overlap, insert the prefetch
-        const int plo = (k > kstop) ? qg - 1 : 0;
-        const int np = w - plo;
-        for (int e = tid; e < np * NR; e += NT) {
-            const int p = plo + e / NR, re = e % NR;
-            const int c = c0 + p, xr = x0 + re;
-            if (c <= n && xr <= n) X[AT(ld, xr, c)] = buf[p * LDS + re];
-        }
-        if (k > kstop) {
-            __syncthreads();
-            for (int e = tid; e < (qg - 1) * NR; e += NT) {
-                const int p = e / NR, re = e % NR;
-                buf[(p + r) * LDS + re] = buf[p * LDS + re];
-            }
-            __syncthreads();
-#pragma unroll
-            for (int t = 0; t < kPrefetch; ++t) {
-                const int e = tid + t * NT;
-                const int p = e / NR, re = e % NR;
-                if (p < r) buf[p * LDS + re] = pre[t];
-            }
-            __syncthreads();
-        }
-    }
+    right_window_rows<NT>(a.M[mi], a.ld[mi], kind, (kind == 3) ? a.R.VQ : a.R.VZ, (kind == 3) ? a.R.TQ : a.R.TZ,
+                          a.R.kdim, n, r, j1, qg, x0, kmax, kstop, sm);
 }
 
 // ---------------------------------------------------------------------------------------
