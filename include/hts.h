@@ -121,7 +121,8 @@ hts_status hts_reduce_stage1(hts_ctx *ctx, int n, int r,
  * reflectors one at a time in native FP64; HTS_GEMM_EMU_BF16 forms each block's reflector
  * product U_k (w x w, w = r + q - 1) and applies it as a product emulated on the BF16 tensor
  * cores (8 base-256 digits per operand, FP32 accumulation of exact integer partial sums,
- * result error below 2^-58 of each row window's largest entry); it requires r = 16
+ * error of each product below 2^-55 of the power of two above the window's largest entry,
+ * about 2^-58 typically); it requires r = 16
  * (HTS_ERR_UNSUPPORTED otherwise).  The chase runs in native FP64 in both modes.
  */
 hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r,

@@ -17,10 +17,12 @@
 // is the sum over digit pairs (i, t) of (digits_i of the rows) (digits_t of U_k), weighted by
 // 256^-(i+t); pairs with the same level i + t share an FP32 accumulator, in which every partial
 // sum is an integer below 2^22 and hence exact.  Levels 2..9 are formed (36 products, each a
-// 16 x 8 x 16 BF16 mma.sync) and summed in 64-bit integer arithmetic; the dropped levels
-// weigh less than 2^-58 of the row's largest entry.  Row scales are powers of two taken from
-// the largest entry of each row window; U_k (orthogonal, entries in [-1, 1]) uses the fixed
-// scale 2^-61.  No FP64 instruction runs in the update loop: FP64 values enter and leave
+// 16 x 8 x 16 BF16 mma.sync) and summed in 64-bit integer arithmetic.  Row scales are powers of
+// two taken from the largest entry of each row window (2^e > max |a|, a = x 2^(e-62)); U_k
+// (orthogonal, entries in [-1, 1]) uses the fixed scale 2^-61.  The error of a product is
+// below 2^(e-55): U's rounding contributes at most 2^-62 sum |a_k|, the dropped levels about
+// 2^(e-58) for typical digits (2^(e-53) for adversarial ones), far below one FP64 rounding unit
+// of the window's largest entry.  No FP64 instruction runs in the update loop: FP64 values enter and leave
 // through integer bit manipulation of their IEEE-754 encoding.
 #include "right_window.cuh"
 
