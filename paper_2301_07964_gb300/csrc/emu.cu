@@ -310,10 +310,8 @@ __device__ __forceinline__ void emu_worker(const EmuArgs &a, EmuSmem &S, int kin
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
 #pragma unroll
-                    for (int pr = 0; pr < 2; ++pr) {
+                    for (int pr = 0; pr < 2; ++pr)
                         S.carry[slab][(rr * 2 + h) * 2 + pr][lane] = refix(xc[rr][h][pr], uc[rr], ua[rr]);
-                        xv[rr][h][pr] = f64_to_fixed(dv[rr][h][pr], ua[rr]);
-                    }
             }
         }
         named_barrier(bar, 64);
@@ -327,7 +325,14 @@ __device__ __forceinline__ void emu_worker(const EmuArgs &a, EmuSmem &S, int kin
                     for (int pr = 0; pr < 2; ++pr) xv[rr][h][pr] = S.carry[slab][(rr * 2 + h) * 2 + pr][lane];
             }
         } else {
-            // the next window's new columns (positions 0 .. r-1)
+            // this window's new columns in fixed point (after the hand-off, so that half 1 is
+            // not kept waiting), then the next window's new columns (positions 0 .. r-1)
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int pr = 0; pr < 2; ++pr) xv[rr][h][pr] = f64_to_fixed(dv[rr][h][pr], ua[rr]);
 #pragma unroll
             for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
