@@ -34,7 +34,7 @@ constexpr int kDigits = 8;                 // balanced base-256 digits per opera
 constexpr int kTopLevel = 9;               // digit pairs with i + t <= 9 are formed
 constexpr int kPlaneWords = kDigits * 2 * 4 * 32;   // uint2 words of one U_k (16 KiB)
 constexpr int kUnitU = -61;                // U_k entries as integers round(u 2^61)
-constexpr int kEmuWarps = 4;               // 16-line slabs per apply block
+constexpr int kEmuWarps = 2;               // 16-line slabs per apply block
 constexpr int kEmuRows = 16 * kEmuWarps;   // rows (or columns) per apply block
 constexpr int kZeroExp = -4000;            // "exponent" of a zero value
 
@@ -204,8 +204,9 @@ __global__ void __launch_bounds__(128) k_s2_form_u(FormUArgs a)
 }
 
 // ---------------------------------------------------------------------------------------
-// Emulated delayed update.  A block owns 64 lines (rows of X for the right updates, columns
-// of X for the left updates) in four slabs of 16, and each slab's window of 32 positions
+// Emulated delayed update.  A block owns 32 lines (rows of X for the right updates, columns
+// of X for the left updates) in two slabs of 16 (small blocks, so that several run on one SM
+// out of phase with each other), and each slab's window of 32 positions
 // (window index p = column c0 + p, or row R0 + p, with c0 = R0 = j1 + k r + 1).  Two warps
 // share a slab: half 0 holds positions 0..15 (operand k-tile 0), half 1 positions 16..31.
 // Lane 4 g + c holds lines g and g + 8 at positions 16 kt + 8 h + 2 c + {0, 1}: exactly the

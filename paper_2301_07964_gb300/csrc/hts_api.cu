@@ -127,7 +127,7 @@ GroupCost s2_group_cost(int n, int r, int j1, int qg, bool hasQ, bool hasZ, bool
     GroupCost c{};
     const int jl = j1 + qg - 1;
     const int kmax = nblocks_gen(n, r, j1) - 1;
-    const int er = 64;   // rows per tile of the emulated right update
+    const int er = 32;   // rows per tile of the emulated right update
     for (int j = j1; j <= jl; ++j) {
         const int kg = nblocks_gen(n, r, j);
         for (int k = 0; k < kg; ++k) {
@@ -182,8 +182,8 @@ GroupCost s2_group_cost(int n, int r, int j1, int qg, bool hasQ, bool hasZ, bool
         }
     c.b_left = 16.0 * le;
     if (emu) {
-        // tensor-core work: 288 mma.m16n8k16 (4096 flops each) per warp and window step
-        const double step = 4.0 * 288.0 * 4096.0;   // one 64-line tile (4 warps)
+        // tensor-core work: 288 mma.m16n8k16 (4096 flops each) per 16-line slab and window step
+        const double step = (er / 16) * 288.0 * 4096.0;   // one tile: 288 mma per 16-line slab
         const int ntile = (n + er - 1) / er;
         for (int t = 0; t < ntile; ++t) {
             const int l0 = t * er + 1, llast = imin(l0 + er - 1, n);
