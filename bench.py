@@ -51,6 +51,23 @@ def paper_flops(n):
     return 10.0 * float(n) ** 3
 
 
+def chase_floor_ms(n, r, q, mhz):
+    """Latency floor of the chase: the steps on each group's critical path (the last sweep's
+    blocks plus the 3-block lag of each earlier sweep) times the dependent FP64 instructions of
+    one step of the last sweep, 64 cycles each (one FP64 warp instruction occupies its SM
+    sub-partition's FP64 unit for 64 cycles).  Per step (r = 16 kernel): 15 RQ reflectors of
+    23 dependent instructions (two 16-lane reductions, the update of the next pivot row, the
+    square root and the scaled-reflector scalars), 24 each for Q^ and Z^, 18 for the band
+    update and 39 for the last sweep's aggregated lazy updates."""
+    chain = (r - 1) * 23 + 2 * 24 + 18 + 39
+    steps = 0
+    for j1 in range(1, n - 1, q):
+        qg = min(q, n - 2 - j1 + 1)
+        jl = j1 + qg - 1
+        steps += (2 + (n - jl - 1) // r) + 3 * (qg - 1)
+    return steps * chain * 64 / (mhz * 1e3)
+
+
 def sweep_work(n, r):
     """Direct flop count of each sweep of Alg. 2 (4 flops per element and reflector), used to
     scale a bounded oracle sample to its share of the whole stage."""
@@ -231,6 +248,18 @@ def run_reference(args, n, r):
 # ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
+def chase_floor(prof, n, r, q, clk, steps):
+    """The chase's time against its dependent-FP64-chain floor (chase_floor_ms)."""
+    name = "k_s2_chase16" if r <= 16 else "k_s2_generate"
+    if name not in prof or r > 16:
+        return None
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    floor = chase_floor_ms(n, r, q, mhz)
+    ms = prof[name]["ms"] / steps
+    return {"kernel": name, "floor_ms": floor, "measured_ms": ms, "frac": floor / ms, "sm_mhz": mhz,
+            "model": "critical-path steps x dependent FP64 instructions per step x 64 cycles"}
+
+
 def run_ours(args, n, r):
     import torch
     ws, rank, local = dist_env()
@@ -397,6 +426,7 @@ def run_ours(args, n, r):
         "gpu_launches": int(sum(v["launches"] for v in prof.values())),
         "profile_dropped": dropped,
         "roofline": roofline,
+        "chase_floor": chase_floor(prof, n, r, q, clk, args.steps),
         "kernels": kernels,
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
         "wall_s_timed": t_wall,
