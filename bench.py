@@ -56,10 +56,11 @@ def chase_floor_ms(n, r, q, mhz):
     blocks plus the 3-block lag of each earlier sweep) times the dependent FP64 instructions of
     one step of the last sweep, 64 cycles each (one FP64 warp instruction occupies its SM
     sub-partition's FP64 unit for 64 cycles).  Per step (r = 16 kernel): 15 RQ reflectors of
-    23 dependent instructions (two 16-lane reductions, the update of the next pivot row, the
-    square root and the scaled-reflector scalars), 24 each for Q^ and Z^, 18 for the band
-    update and 39 for the last sweep's aggregated lazy updates."""
-    chain = (r - 1) * 23 + 2 * 24 + 18 + 39
+    18 dependent instructions (one 16-lane reduction that forms u.y and |y|^2 together, the
+    update of the next pivot row, its downdated norm, the square root and the scaled-reflector
+    scalars), 24 each for Q^ and Z^, 18 for the band update and 39 for the last sweep's
+    aggregated lazy updates."""
+    chain = (r - 1) * 18 + 2 * 24 + 18 + 39
     steps = 0
     for j1 in range(1, n - 1, q):
         qg = min(q, n - 2 - j1 + 1)

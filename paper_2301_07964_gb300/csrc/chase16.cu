@@ -54,8 +54,8 @@ __device__ __forceinline__ double sum16(double v)
 
 __device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong(v) << 1) == 0; }
 
-// nxo (sum of squares below the pivot) and alpha (pivot) far from over- and underflow;
-// tested on the exponent bits.
+// A sum of squares nxo and the pivot alpha far from over- and underflow; tested on the exponent
+// bits.
 __device__ __forceinline__ bool safe_sums(double nxo, double alpha)
 {
     const int en = (__double2hiint(nxo) >> 20) & 0x7ff;
@@ -109,11 +109,12 @@ __device__ __forceinline__ double panel_house(double x, int c, int piv, int len,
     return (c == piv) ? up : ((c < len) ? x : 0.0);
 }
 
-// 2^-e and 2^(1-e) for the binary exponent e of a positive normal d.
-__device__ __forceinline__ void pow2_scale(double d, double *s, double *s2)
+// For a positive normal d = f 2^e with f in [1, 2): *s1 = f (d's significand, by bit
+// arithmetic rather than a multiplication on the FP64 unit) and *s2 = 2^(1-e).
+__device__ __forceinline__ void pow2_scale(double d, double *s1, double *s2)
 {
-    const int eb = (__double2hiint(d) >> 20) & 0x7ff;
-    *s = __hiloint2double((2046 - eb) << 20, 0);
+    const int hi = __double2hiint(d), eb = (hi >> 20) & 0x7ff;
+    *s1 = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(d));
     *s2 = __hiloint2double((2047 - eb) << 20, 0);
 }
 
@@ -469,11 +470,7 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
                 int esc;
                 bool ident;
                 u = panel_house(x, c, piv, piv + 1, &beta, &un2, &esc, &ident);
-                if (!ident) {
-                    double sc;
-                    pow2_scale(un2, &sc, &sc2);
-                    s1 = un2 * sc;
-                }
+                if (!ident) pow2_scale(un2, &s1, &sc2);
                 if (lane < kM) hu[0][lane] = u;
                 if (lane == 0) {
                     hs[0][0] = s1;
@@ -485,22 +482,44 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
                 const int piv = m - 1 - t, cur = t & 1;
                 if (warp == 0) {
                     if (piv >= 2) {
-                        // next pivot row: apply reflector t, then form reflector t+1 from it
+                        // next pivot row y (columns 0 .. piv): apply reflector t, then form
+                        // reflector t+1 from y'(0 .. piv-1).  The scaled reflector multiplies
+                        // norms by s1 and leaves y'_piv final, so |y'(0 .. piv-1)|^2 =
+                        // s1^2 |y|^2 - y'_piv^2: the upper half-warp sums |y|^2 in the same
+                        // instructions that sum u.y in the lower half, which takes the second
+                        // reduction off the chain.  Where that difference loses more than two bits
+                        // to cancellation, or the sums approach over- or underflow, the reflector
+                        // is formed from y' directly.  The part below the pivot, nx - alpha^2,
+                        // only enters |u|^2 >= nx, so its absolute error (a few ulps of nx)
+                        // perturbs the reflector by a few ulps relative to the entries it
+                        // annihilates.  When those entries are zero the reflector changes the sign
+                        // of the pivot coordinate only; G's zeros stay exact and the direction of
+                        // G(:, 1), all that the RQ is used for, keeps its value up to sign.
+                        const bool hi = lane >= 16;
+                        const double a1 = (s1 != 0.0) ? s1 : 1.0, a2 = (s1 != 0.0) ? sc2 : 0.0;
                         double y = (c <= piv) ? W[(piv - 1) * kLD + c] : 0.0;
-                        if (s1 != 0.0) {
-                            const double cf = sum16(y * u) * sc2;
-                            y = fma(-cf, u, s1 * y);
-                        }
+                        const double h = sum16(y * (hi ? y : u)) * (hi ? a1 * a1 : a2);
+                        const double hx = __shfl_xor_sync(kFull, h, 16);
+                        y = fma(-(hi ? hx : h), u, a1 * y);
+                        const double S = hi ? h : hx;
+                        const double ypiv = __shfl_sync(kFull, y, piv);
+                        const double alpha = __shfl_sync(kFull, y, piv - 1);
+                        const double nx = fma(-ypiv, ypiv, S), nxo = fma(-alpha, alpha, nx);
                         double beta, un2;
                         int esc;
                         bool ident;
-                        u = panel_house(y, c, piv - 1, piv, &beta, &un2, &esc, &ident);
-                        s1 = 0.0;
-                        if (!ident) {
-                            double sc;
-                            pow2_scale(un2, &sc, &sc2);
-                            s1 = un2 * sc;
+                        if (safe_sums(nx, alpha) &&
+                            __double_as_longlong(nx) >= __double_as_longlong(S) - (2ll << 52)) {
+                            const double nrm = nx * rsqrt(nx);
+                            const double up = alpha - neg_sign_of(alpha, nrm);
+                            un2 = fma(up, up, nxo);
+                            u = (c == piv - 1) ? up : ((c < piv) ? y : 0.0);
+                            ident = false;
+                        } else {
+                            u = panel_house(y, c, piv - 1, piv, &beta, &un2, &esc, &ident);
                         }
+                        s1 = 0.0;
+                        if (!ident) pow2_scale(un2, &s1, &sc2);
                         if (lane < kM) hu[cur ^ 1][lane] = u;
                         if (lane == 0) {
                             hs[cur ^ 1][0] = s1;
