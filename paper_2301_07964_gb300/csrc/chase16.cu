@@ -203,6 +203,62 @@ __device__ __forceinline__ void rq_bulk(double *W, double *G, const double *hu, 
     }
 }
 
+// One step of the column elimination on the panel row x (lane c holds x_c, both half-warps
+// the same).  Returns the pivot p, the active column of largest |x_c| (compared on the high
+// word of the encoding, so within a factor 1 + 2^-20 of the largest), or -1 when the row
+// vanishes on the active columns; sets a = x_p 2^-e (x_p's sign, |a| in [1, 2)) and
+// b_c = x_c 2^-e, with 2^e the power of two of x_p (b_c = 0 for c = p, inactive columns and
+// entries below 2^(e-1022), whose share is far below rounding).  Column c then becomes
+// a col_c - b_c col_p, which clears x_c up to rounding with multipliers |b_c / a| <= 1 + 2^-19.
+// No FP64 instruction: integer maximum, ballot and bit arithmetic.  *bad: x_p outside
+// [2^-959, 2^960], where the growth of at most 4 per step could leave the exponent range.
+__device__ __forceinline__ int elim_step(double x, unsigned act, int c, double *a, double *b, bool *bad)
+{
+    const bool on = (act >> c) & 1u;
+    const int hx = __double2hiint(x);
+    const unsigned key = on ? (unsigned)(hx & 0x7fffffff) : 0u;
+    const unsigned kmax = __reduce_max_sync(kFull, key);
+    *a = 1.0;
+    *b = 0.0;
+    *bad = false;
+    if (kmax == 0u) return -1;
+    const int p = __ffs(__ballot_sync(kFull, key == kmax) & 0xffffu) - 1;
+    const int hp = __shfl_sync(kFull, hx, p), lp = __shfl_sync(kFull, __double2loint(x), p);
+    const int ebp = (hp >> 20) & 0x7ff;
+    *bad = ebp < 64 || ebp > 1983;
+    *a = __hiloint2double((hp & 0x800fffff) | 0x3ff00000, lp);
+    const int ebx = (hx >> 20) & 0x7ff, ebn = ebx - ebp + 1023;
+    if (on && c != p && ebx != 0 && ebn >= 1)
+        *b = __hiloint2double((hx & 0x800fffff) | (ebn << 20), __double2loint(x));
+    return p;
+}
+
+// Bulk of one elimination step: column c of W rows 0 .. rho-2 and of G becomes
+// a col_c - b_c col_p for the active columns c != p.  Lane i takes row i (the W rows, then the
+// G rows; at most 14 + 16), warp bw every third such column (at most 5).
+__device__ __forceinline__ void elim_bulk(double *W, double *G, const double *b, double a, int p, unsigned act,
+                                          int rho, int m, int bw, int lane)
+{
+    const int nw = rho - 1;
+    const bool own = lane < nw + m;
+    double *rowp = (lane < nw) ? &W[lane * kLD] : &G[(lane - nw) * kLD];
+    unsigned cs = act & ~(1u << p), mine = 0u;
+    for (int k = 0; cs != 0u; cs &= cs - 1u, k = (k == 2) ? 0 : k + 1)
+        if (k == bw) mine |= cs & (0u - cs);
+    const double vp = own ? rowp[p] : 0.0;
+    int ci[5];
+    double v[5];
+#pragma unroll
+    for (int e = 0; e < 5; ++e) {
+        ci[e] = mine ? __ffs(mine) - 1 : -1;
+        mine &= mine - 1u;
+        v[e] = (own && ci[e] >= 0) ? rowp[ci[e]] : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < 5; ++e)
+        if (own && ci[e] >= 0) rowp[ci[e]] = fma(-b[ci[e]], vp, a * v[e]);
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
@@ -220,6 +276,14 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
     __shared__ double pu[kM];              // current Q^ / Z^ vector
     __shared__ double ps[2];               // {tau applied to the unscaled data, beta}
     __shared__ double vv[kM];              // helper block: current reflector
+    __shared__ double eb[2][kM];           // elimination steps: multipliers b (double buffered)
+    __shared__ double ea[2];               // ... and a
+    __shared__ int ep[2];                  // ... pivot column (-1: the row vanished)
+    __shared__ unsigned eact[2];           // ... active columns, pivot included
+    __shared__ int s_ew[2];                // biased exponent of max |W| (the B block after Q^)
+    __shared__ int s_ez;                   // biased exponent of max |z|
+    __shared__ int s_cs;                   // column of G that holds z
+    __shared__ int s_redo;                 // the elimination failed its checks: use the RQ
     __shared__ int s_abort;
 
     const bool helper = (int)blockIdx.x >= a.qg;
@@ -244,7 +308,10 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
         TQs[k] = 0.0;
         TZs[k] = 0.0;
     }
-    if (tid == 0) s_abort = __ldcg(a.status) != 0;   // an earlier kernel of this call failed
+    if (tid == 0) {
+        s_abort = __ldcg(a.status) != 0;   // an earlier kernel of this call failed
+        s_redo = 0;
+    }
     __syncthreads();
     if (s_abort) return;
     unsigned long long *hflags = a.flags + a.qmax;       // progress of the helper blocks
@@ -431,6 +498,7 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
                 if (qown) y0 = qfromb ? bcol[off] : W[qcol];   // read before any lane rewrites row 0
             }
             __syncthreads();
+            unsigned wkey = 0u;
             if (qown) {
                 const double tau = ps[0], beta = ps[1];
                 const double cf = tau != 0.0 ? fma(-beta, y0, pdot) * tau : 0.0;
@@ -441,8 +509,14 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
                         const double v = fma(-cf, pu[i], y[e]);
                         W[i * kLD + qcol] = v;
                         Wq[i * kLD + qcol] = v;
+                        const unsigned vk = (unsigned)(__double2hiint(v) & 0x7fffffff);
+                        wkey = vk > wkey ? vk : wkey;
                     }
                 }
+            }
+            if (warp == 1 || warp == 2) {
+                wkey = __reduce_max_sync(kFull, wkey);
+                if (lane == 0) s_ew[warp - 1] = (int)(wkey >> 20);
             }
             if (warp == 0 && ps[0] != 0.0 && lane < m) col[off + lane] = (lane == 0) ? ps[1] : 0.0;
             __syncthreads();
@@ -460,158 +534,245 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
             if (k + 1 < kl) load_lazy(a, k + 1, nlazy, lvb[(k + 1) & 1], ltb[(k + 1) & 1], grb[(k + 1) & 1], lane, 32);
         }
 
-        // ---- 4. RQ of the B block with look-ahead (warps 0 .. 3)
-        if (gen && m >= 2 && warp < 4) {
-            double u = 0.0, s1 = 0.0, sc2 = 0.0;   // panel: current reflector
-            if (warp == 0) {
-                const int piv = m - 1;
-                const double x = (c <= piv) ? W[piv * kLD + c] : 0.0;
-                double beta, un2;
-                int esc;
-                bool ident;
-                u = panel_house(x, c, piv, piv + 1, &beta, &un2, &esc, &ident);
-                if (!ident) pow2_scale(un2, &s1, &sc2);
-                if (lane < kM) hu[0][lane] = u;
-                if (lane == 0) {
-                    hs[0][0] = s1;
-                    hs[0][1] = sc2;
+        // ---- 4. the direction z of the opposite reflector, W z = lambda e_1 (warps 0 .. 3), and
+        // ---- 5. Z^ from z with the band update.  Attempt 0 finds z by column elimination with
+        //      partial pivoting (W M upper triangular up to a column order; z is the column of M
+        //      that no step retired): its chain per row is an integer pivot search and one
+        //      multiply-add, where each RQ reflector needs a reduction and a square root.  The
+        //      band dots of the block rows below the first are the entries Z^ zeroes, (W z)_i;
+        //      if one exceeds 2^-44 max|W| max|z|, or a pivot leaves the safe exponent range,
+        //      nothing is written and attempt 1 takes z from the RQ of W (Alg. 3's opposite
+        //      reflector: the first column of the RQ's accumulated right factor).
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            if (attempt == 1) {
+                for (int e = tid; e < m * m; e += kGenThreads) {
+                    const int i = e / m, cc = e % m;
+                    W[i * kLD + cc] = Wq[i * kLD + cc];
+                    G[i * kLD + cc] = (i == cc) ? 1.0 : 0.0;
                 }
+                __syncthreads();
+                if (tid == 0) {
+                    s_redo = 0;
+                    s_cs = 0;
+                }
+            } else if (tid == 0) {
+                s_cs = 0;
             }
-            named_barrier(1, 128);
-            for (int t = 0; t + 1 < m; ++t) {
-                const int piv = m - 1 - t, cur = t & 1;
-                if (warp == 0) {
-                    if (piv >= 2) {
-                        // next pivot row y (columns 0 .. piv): apply reflector t, then form
-                        // reflector t+1 from y'(0 .. piv-1).  The scaled reflector multiplies
-                        // norms by s1 and leaves y'_piv final, so |y'(0 .. piv-1)|^2 =
-                        // s1^2 |y|^2 - y'_piv^2: the upper half-warp sums |y|^2 in the same
-                        // instructions that sum u.y in the lower half, which takes the second
-                        // reduction off the chain.  Where that difference loses more than two bits
-                        // to cancellation, or the sums approach over- or underflow, the reflector
-                        // is formed from y' directly.  The part below the pivot, nx - alpha^2,
-                        // only enters |u|^2 >= nx, so its absolute error (a few ulps of nx)
-                        // perturbs the reflector by a few ulps relative to the entries it
-                        // annihilates.  When those entries are zero the reflector changes the sign
-                        // of the pivot coordinate only; G's zeros stay exact and the direction of
-                        // G(:, 1), all that the RQ is used for, keeps its value up to sign.
-                        const bool hi = lane >= 16;
-                        const double a1 = (s1 != 0.0) ? s1 : 1.0, a2 = (s1 != 0.0) ? sc2 : 0.0;
-                        double y = (c <= piv) ? W[(piv - 1) * kLD + c] : 0.0;
-                        const double h = sum16(y * (hi ? y : u)) * (hi ? a1 * a1 : a2);
-                        const double hx = __shfl_xor_sync(kFull, h, 16);
-                        y = fma(-(hi ? hx : h), u, a1 * y);
-                        const double S = hi ? h : hx;
-                        const double ypiv = __shfl_sync(kFull, y, piv);
-                        const double alpha = __shfl_sync(kFull, y, piv - 1);
-                        const double nx = fma(-ypiv, ypiv, S), nxo = fma(-alpha, alpha, nx);
+            if (gen && m >= 2 && warp < 4) {
+                if (attempt == 0) {
+                    unsigned act = (1u << m) - 1u;   // panel: active columns, current step
+                    int p = -1;
+                    double a = 1.0, b = 0.0;
+                    bool bad = false;
+                    if (warp == 0) {
+                        const double x = (c < m) ? W[(m - 1) * kLD + c] : 0.0;
+                        p = elim_step(x, act, c, &a, &b, &bad);
+                        if (lane < kM) eb[0][lane] = b;
+                        if (lane == 0) {
+                            ea[0] = a;
+                            ep[0] = p;
+                            eact[0] = act;
+                            if (bad) s_redo = 1;
+                        }
+                    }
+                    named_barrier(1, 128);
+                    for (int t = 0; t + 1 < m; ++t) {
+                        const int rho = m - 1 - t, cur = t & 1;
+                        if (warp == 0) {
+                            if (rho >= 2) {
+                                // row rho-1 under step t (look-ahead), then step t+1 on it
+                                double y = (c < m) ? W[(rho - 1) * kLD + c] : 0.0;
+                                if (p >= 0) {
+                                    const double yn = fma(-b, __shfl_sync(kFull, y, p), a * y);
+                                    if (((act >> c) & 1u) && c != p) y = yn;
+                                    act &= ~(1u << p);
+                                }
+                                p = elim_step(y, act, c, &a, &b, &bad);
+                                if (lane < kM) eb[cur ^ 1][lane] = b;
+                                if (lane == 0) {
+                                    ea[cur ^ 1] = a;
+                                    ep[cur ^ 1] = p;
+                                    eact[cur ^ 1] = act;
+                                    if (bad) s_redo = 1;
+                                }
+                            }
+                        } else {
+                            // bulk: step t on W rows 0 .. rho-2 and on G
+                            const int pt = ep[cur];
+                            if (pt >= 0) elim_bulk(W, G, eb[cur], ea[cur], pt, eact[cur], rho, m, warp - 1, lane);
+                        }
+                        named_barrier(1, 128);
+                    }
+                    // the one column no step retired (the lowest, if rows vanished)
+                    if (warp == 0 && lane == 0) s_cs = __ffs(p >= 0 ? act & ~(1u << p) : act) - 1;
+                } else {
+                    // RQ of the B block with look-ahead
+                    double u = 0.0, s1 = 0.0, sc2 = 0.0;   // panel: current reflector
+                    if (warp == 0) {
+                        const int piv = m - 1;
+                        const double x = (c <= piv) ? W[piv * kLD + c] : 0.0;
                         double beta, un2;
                         int esc;
                         bool ident;
-                        if (safe_sums(nx, alpha) &&
-                            __double_as_longlong(nx) >= __double_as_longlong(S) - (2ll << 52)) {
-                            const double nrm = nx * rsqrt(nx);
-                            const double up = alpha - neg_sign_of(alpha, nrm);
-                            un2 = fma(up, up, nxo);
-                            u = (c == piv - 1) ? up : ((c < piv) ? y : 0.0);
-                            ident = false;
-                        } else {
-                            u = panel_house(y, c, piv - 1, piv, &beta, &un2, &esc, &ident);
-                        }
-                        s1 = 0.0;
+                        u = panel_house(x, c, piv, piv + 1, &beta, &un2, &esc, &ident);
                         if (!ident) pow2_scale(un2, &s1, &sc2);
-                        if (lane < kM) hu[cur ^ 1][lane] = u;
+                        if (lane < kM) hu[0][lane] = u;
                         if (lane == 0) {
-                            hs[cur ^ 1][0] = s1;
-                            hs[cur ^ 1][1] = sc2;
+                            hs[0][0] = s1;
+                            hs[0][1] = sc2;
                         }
                     }
-                } else {
-                    // bulk: W rows 0 .. piv-2 and G rows 0 .. m-1, three lanes per row, only the
-                    // live columns 0 .. piv; a warp without rows skips the step
-                    const double bs1 = hs[cur][0];
-                    const int bw = warp - 1;
-                    if (bs1 != 0.0 && bw * 10 < (piv - 1) + m) {
-                        const double bsc2 = hs[cur][1];
-                        switch ((piv + 3) / 3) {
-                        case 6: rq_bulk<6>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
-                        case 5: rq_bulk<5>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
-                        case 4: rq_bulk<4>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
-                        case 3: rq_bulk<3>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
-                        case 2: rq_bulk<2>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
-                        default: rq_bulk<1>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
+                    named_barrier(1, 128);
+                    for (int t = 0; t + 1 < m; ++t) {
+                        const int piv = m - 1 - t, cur = t & 1;
+                        if (warp == 0) {
+                            if (piv >= 2) {
+                                // next pivot row y (columns 0 .. piv): apply reflector t, then form
+                                // reflector t+1 from y'(0 .. piv-1).  The scaled reflector multiplies
+                                // norms by s1 and leaves y'_piv final, so |y'(0 .. piv-1)|^2 =
+                                // s1^2 |y|^2 - y'_piv^2: the upper half-warp sums |y|^2 in the same
+                                // instructions that sum u.y in the lower half, which takes the second
+                                // reduction off the chain.  Where that difference loses more than two bits
+                                // to cancellation, or the sums approach over- or underflow, the reflector
+                                // is formed from y' directly.  The part below the pivot, nx - alpha^2,
+                                // only enters |u|^2 >= nx, so its absolute error (a few ulps of nx)
+                                // perturbs the reflector by a few ulps relative to the entries it
+                                // annihilates.  When those entries are zero the reflector changes the sign
+                                // of the pivot coordinate only; G's zeros stay exact and the direction of
+                                // G(:, 1), all that the RQ is used for, keeps its value up to sign.
+                                const bool hi = lane >= 16;
+                                const double a1 = (s1 != 0.0) ? s1 : 1.0, a2 = (s1 != 0.0) ? sc2 : 0.0;
+                                double y = (c <= piv) ? W[(piv - 1) * kLD + c] : 0.0;
+                                const double h = sum16(y * (hi ? y : u)) * (hi ? a1 * a1 : a2);
+                                const double hx = __shfl_xor_sync(kFull, h, 16);
+                                y = fma(-(hi ? hx : h), u, a1 * y);
+                                const double S = hi ? h : hx;
+                                const double ypiv = __shfl_sync(kFull, y, piv);
+                                const double alpha = __shfl_sync(kFull, y, piv - 1);
+                                const double nx = fma(-ypiv, ypiv, S), nxo = fma(-alpha, alpha, nx);
+                                double beta, un2;
+                                int esc;
+                                bool ident;
+                                if (safe_sums(nx, alpha) &&
+                                    __double_as_longlong(nx) >= __double_as_longlong(S) - (2ll << 52)) {
+                                    const double nrm = nx * rsqrt(nx);
+                                    const double up = alpha - neg_sign_of(alpha, nrm);
+                                    un2 = fma(up, up, nxo);
+                                    u = (c == piv - 1) ? up : ((c < piv) ? y : 0.0);
+                                    ident = false;
+                                } else {
+                                    u = panel_house(y, c, piv - 1, piv, &beta, &un2, &esc, &ident);
+                                }
+                                s1 = 0.0;
+                                if (!ident) pow2_scale(un2, &s1, &sc2);
+                                if (lane < kM) hu[cur ^ 1][lane] = u;
+                                if (lane == 0) {
+                                    hs[cur ^ 1][0] = s1;
+                                    hs[cur ^ 1][1] = sc2;
+                                }
+                            }
+                        } else {
+                            // bulk: W rows 0 .. piv-2 and G rows 0 .. m-1, three lanes per row, only the
+                            // live columns 0 .. piv; a warp without rows skips the step
+                            const double bs1 = hs[cur][0];
+                            const int bw = warp - 1;
+                            if (bs1 != 0.0 && bw * 10 < (piv - 1) + m) {
+                                const double bsc2 = hs[cur][1];
+                                switch ((piv + 3) / 3) {
+                                case 6: rq_bulk<6>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
+                                case 5: rq_bulk<5>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
+                                case 4: rq_bulk<4>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
+                                case 3: rq_bulk<3>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
+                                case 2: rq_bulk<2>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
+                                default: rq_bulk<1>(W, G, hu[cur], bs1, bsc2, piv, m, bw, lane); break;
+                                }
+                            }
                         }
+                        named_barrier(1, 128);
                     }
                 }
-                named_barrier(1, 128);
             }
-        }
-        __syncthreads();
+            __syncthreads();
 
-        // warp 4 takes the next step's dependencies while Z^ and the band update run
-        if (tid == 128 && s > 0 && k + 1 < kl) s_abort = !wait_deps(k + 1);
+            // warp 4 takes the next step's dependencies while Z^ and the band update run
+            if (attempt == 0 && tid == 128 && s > 0 && k + 1 < kl) s_abort = !wait_deps(k + 1);
 
-        if (gen) {
-            // ---- 5. opposite reflector Z^ from G(:, 1) (panel); band dots (warps 5 .. 7)
-            double p = 0.0;
-            const bool band = bt >= 0 && bt < nband;
-            const bool isA = bt < na;
-            const int xrow = isA ? x0 + bt : x0 + (bt - na);
-            if (warp == 0) {
-                const double x = (c < m) ? G[c * kLD] : 0.0;
-                double beta, un2;
-                int esc;
-                bool ident;
-                const double u = panel_house(x, c, 0, m, &beta, &un2, &esc, &ident);
-                const double tau = ident ? 0.0 : 2.0 * __drcp_rn(un2);
-                if (lane < kM) pu[lane] = u;
-                if (lane == 0) {
-                    ps[0] = ident ? 0.0 : (esc ? scalbn(tau, -esc) : tau);
-                    ps[1] = ident ? beta : (esc ? scalbn(beta, esc) : beta);
-                    TZs[k] = tau;
-                }
-                if (lane < r) VZs[(size_t)k * r + lane] = (!ident && lane < m) ? u : 0.0;
-            } else if (band) {
-                if (bt >= na + nbt) {
-                    const int bi = bt - na - nbt;
+            if (gen) {
+                // ---- 5. opposite reflector Z^ from z = G(:, cs) (panel); band dots (warps 5 .. 7)
+                const int cs = s_cs;
+                double p = 0.0;
+                const bool band = bt >= 0 && bt < nband;
+                const bool isA = bt < na;
+                const int xrow = isA ? x0 + bt : x0 + (bt - na);
+                if (warp == 0) {
+                    const double x = (c < m) ? G[c * kLD + cs] : 0.0;
+                    double beta, un2;
+                    int esc;
+                    bool ident;
+                    const double u = panel_house(x, c, 0, m, &beta, &un2, &esc, &ident);
+                    const double tau = ident ? 0.0 : 2.0 * __drcp_rn(un2);
+                    if (lane < kM) pu[lane] = u;
+                    if (lane == 0) {
+                        ps[0] = ident ? 0.0 : (esc ? scalbn(tau, -esc) : tau);
+                        ps[1] = ident ? beta : (esc ? scalbn(beta, esc) : beta);
+                        TZs[k] = tau;
+                    }
+                    if (lane < r) VZs[(size_t)k * r + lane] = (!ident && lane < m) ? u : 0.0;
+                    if (attempt == 0) {
+                        const unsigned zk = __reduce_max_sync(kFull, (unsigned)(__double2hiint(x) & 0x7fffffff));
+                        if (lane == 0) s_ez = (int)(zk >> 20);
+                    }
+                } else if (band) {
+                    if (bt >= na + nbt) {
+                        const int bi = bt - na - nbt;
 #pragma unroll
-                    for (int cc = 0; cc < kM; ++cc) brow[cc] = (cc < m) ? Wq[bi * kLD + cc] : 0.0;
-                } else if (!isA && hasb) {
-                    // the B column cb above the block carries the lazy updates of step 2
-                    const double v = bcol[xrow - rlo];
+                        for (int cc = 0; cc < kM; ++cc) brow[cc] = (cc < m) ? Wq[bi * kLD + cc] : 0.0;
+                    } else if (!isA && hasb) {
+                        // the B column cb above the block carries the lazy updates of step 2
+                        const double v = bcol[xrow - rlo];
+#pragma unroll
+                        for (int cc = 0; cc < kM; ++cc)
+                            if (cc == m - 1) brow[cc] = v;
+                    }
+                    double p0 = 0.0, p1 = 0.0;
+#pragma unroll
+                    for (int cc = 0; cc < kM; cc += 2) {
+                        if (cc < m) p0 = fma(brow[cc], G[cc * kLD + cs], p0);
+                        if (cc + 1 < m) p1 = fma(brow[cc + 1], G[(cc + 1) * kLD + cs], p1);
+                    }
+                    p = p0 + p1;
+                }
+                if (warp == 0 || warp >= 5) named_barrier(2, 128);
+                if (attempt == 0 && warp >= 5) {
+                    // the entries the reflector zeroes, (W z)_i / |z|, for the block rows below the first
+                    if (band && !isA && xrow > g.i1 && !is_zero(p)) {
+                        const int epx = (__double2hiint(p) >> 20) & 0x7ff;
+                        if (epx > imax(s_ew[0], s_ew[1]) + s_ez - 1068) s_redo = 1;
+                    }
+                    named_barrier(3, 96);
+                }
+                if (band && (attempt == 1 || !s_redo)) {
+                    const double tau = ps[0], beta = ps[1];
+                    if (tau != 0.0) {
+                        const double cf = fma(-beta, brow[0], p) * tau;
+#pragma unroll
+                        for (int cc = 0; cc < kM; ++cc) brow[cc] = fma(-cf, pu[cc], brow[cc]);
+                    }
+                    if (!isA && xrow > g.i1) brow[0] = 0.0;   // the reduced column of the B block
+                    double *dst = isA ? A + AT(lda, xrow, g.i1) : B + AT(ldb, xrow, g.i1);
+                    const size_t ld = isA ? (size_t)lda : (size_t)ldb;
 #pragma unroll
                     for (int cc = 0; cc < kM; ++cc)
-                        if (cc == m - 1) brow[cc] = v;
+                        if (cc < m) dst[cc * ld] = brow[cc];
                 }
-                double p0 = 0.0, p1 = 0.0;
-#pragma unroll
-                for (int cc = 0; cc < kM; cc += 2) {
-                    if (cc < m) p0 = fma(brow[cc], G[cc * kLD], p0);
-                    if (cc + 1 < m) p1 = fma(brow[cc + 1], G[(cc + 1) * kLD], p1);
-                }
-                p = p0 + p1;
             }
-            if (warp == 0 || warp >= 5) named_barrier(2, 128);
-            if (band) {
-                const double tau = ps[0], beta = ps[1];
-                if (tau != 0.0) {
-                    const double cf = fma(-beta, brow[0], p) * tau;
-#pragma unroll
-                    for (int cc = 0; cc < kM; ++cc) brow[cc] = fma(-cf, pu[cc], brow[cc]);
-                }
-                if (!isA && xrow > g.i1) brow[0] = 0.0;   // the reduced column of the B block
-                double *dst = isA ? A + AT(lda, xrow, g.i1) : B + AT(ldb, xrow, g.i1);
-                const size_t ld = isA ? (size_t)lda : (size_t)ldb;
-#pragma unroll
-                for (int cc = 0; cc < kM; ++cc)
-                    if (cc < m) dst[cc * ld] = brow[cc];
-            }
+            __syncthreads();
+            if (!s_redo) break;
         }
 
         // ---- 6. publish block k of this sweep; the next step's global loads (its dependencies
         //      were acquired by warp 4 above, and this step's band stores are ordered before
-        //      them by the barrier) are in flight while the stores of this step are fenced
-        __syncthreads();
+        //      them by the barrier above) are in flight while the stores of this step are fenced
         const bool more = k + 1 < kl && !s_abort;
         StepInfo In = I;
         if (more) {
