@@ -3,14 +3,16 @@
 //
 // An FP64 instruction occupies the FP64 unit of its SM sub-partition for about 64 cycles
 // whether 1 or 32 lanes are active, and the four sub-partitions of an SM share little else.
-// The chase is a chain of dependent reflectors, so its length is the number of FP64
-// instructions on that chain.  The block therefore splits roles by sub-partition (warp w runs
-// on sub-partition w mod 4):
-//   warp 0        the panel: every step of the sequential chain (reflector generation, and
-//                 in the RQ the update of the next pivot row), with the lanes as columns;
-//   warps 1 .. 3  bulk updates of the current reflector (other sub-partitions, in parallel);
-//   warp 4        progress waits and global stores (no FP64);
-//   warps 5 .. 7  the band rows of A and B, held in registers (one thread per row).
+// The chase is a chain of dependent steps, so its length is set by the FP64 instructions and
+// warp collectives on that chain.  The block therefore splits roles by sub-partition (warp w
+// runs on sub-partition w mod 4):
+//   warp 0        the panel: every step of the sequential chain (reflector generation, the
+//                 elimination's pivot steps with the update of the next row), lanes as columns;
+//   warps 1 .. 3  bulk updates of the current reflector or elimination step;
+//   warp 4        progress waits; while the elimination runs, the stores of the finished column
+//                 segments and the loads of the next block's lazy data;
+//   warps 5 .. 7  the band rows of A and B, held in registers (one thread per row), and three
+//                 more bulk warps of the elimination.
 //
 // One step (k, j), sweep j waiting as in the general kernel (chase.cu) for block k+2 of sweep
 // j-1 and block k+1 of its helper:
@@ -22,13 +24,16 @@
 //      x -= sum_b d_b u_b (warp 1: pivot column, warp 2: B column);
 //   3. left reflector Q^_k^j from the pivot column (panel) while the bulk warps form the
 //      B block's column dots with it; then the block update;
-//   4. RQ of the B block, last row first, with look-ahead: while the bulk warps apply
-//      reflector t to the remaining rows of W and to G, the panel applies it to the next
-//      pivot row and forms reflector t+1 from it.  RQ reflectors are scaled,
-//      c (|u|^2 I - 2 u u^T) with c a power of two, which needs a square root but no division;
-//      only the direction of G's first column is used and the scaling leaves it unchanged;
-//   5. opposite reflector Z^_k^j from G(:, 1) (panel) while the band threads form their dots
-//      with G(:, 1); then the band update, with B(i1+1:i2, i1) = 0 exactly;
+//   4. the direction z of the opposite reflector: W z parallel to e_1 for the B block W, by
+//      column elimination with partial pivoting, last row first, with look-ahead (the panel
+//      takes step t to the next row and chooses step t+1 there while the bulk warps apply
+//      step t to the other rows of W and to the accumulated column operations G).  Should the
+//      residual check of step 5 fail, the step is repeated with the RQ of W, whose reflectors
+//      are scaled, c (|u|^2 I - 2 u u^T) with c a power of two (a square root but no
+//      division; the scaling leaves the direction of G's first column, the RQ's z, unchanged);
+//   5. opposite reflector Z^_k^j from z (panel) while the band threads form their dots with z
+//      (for the block rows below the first these are the entries Z^ zeroes, checked against
+//      2^-44 max|W| max|z|); then the band update, with B(i1+1:i2, i1) = 0 exactly;
 //   6. publish block k of sweep j.
 // Reflectors are stored as (u, tau) with H = I - tau u u^T, u = x - beta e_1, tau = 2/|u|^2 and
 // beta = -sign(x_1) |x| (the sign of LAPACK's dlarfg); tau = 0 is the identity.
@@ -233,30 +238,30 @@ __device__ __forceinline__ int elim_step(double x, unsigned act, int c, double *
     return p;
 }
 
-// Bulk of one elimination step: column c of W rows 0 .. rho-2 and of G becomes
-// a col_c - b_c col_p for the active columns c != p.  Lane i takes row i (the W rows, then the
-// G rows; at most 14 + 16), warp bw every third such column (at most 5).
-__device__ __forceinline__ void elim_bulk(double *W, double *G, const double *b, double a, int p, unsigned act,
-                                          int rho, int m, int bw, int lane)
+// Bulk of one elimination step: column c of W rows 0 .. rho-2 and of the accumulated column
+// operations G becomes a col_c - b_c col_p, for the active columns c != p (listed in col[0 .. nc-1]).
+// G's column c is zero outside the rows of the retired pivots and its diagonal, and every
+// active column's diagonal is the same product D of the earlier steps' a, so only the G rows
+// ret[0 .. ng-1] take part: the retired pivots in order, then p itself, whose diagonal D stands
+// in for G(p, p).  W rows and G rows are at most m - 1 <= 15: lane i of each half-warp takes
+// row i, the two half-warps the two columns of a pair, warp bw of the six bulk warps every
+// sixth pair.
+__device__ __forceinline__ void elim_bulk(double *W, double *G, const double *b, double a, double D, int p,
+                                          const int *col, int nc, const int *ret, int ng, int rho, int bw,
+                                          int lane)
 {
-    const int nw = rho - 1;
-    const bool own = lane < nw + m;
-    double *rowp = (lane < nw) ? &W[lane * kLD] : &G[(lane - nw) * kLD];
-    unsigned cs = act & ~(1u << p), mine = 0u;
-    for (int k = 0; cs != 0u; cs &= cs - 1u, k = (k == 2) ? 0 : k + 1)
-        if (k == bw) mine |= cs & (0u - cs);
-    const double vp = own ? rowp[p] : 0.0;
-    int ci[5];
-    double v[5];
+    const int i = lane & 15, h = lane >> 4, nw = rho - 1;
+    const bool own = i < nw + ng;
+    double *rowp = (i < nw) ? &W[i * kLD] : &G[(own ? ret[i - nw] : 0) * kLD];
+    const double vp = own ? ((i == nw + ng - 1) ? D : rowp[p]) : 0.0;
 #pragma unroll
-    for (int e = 0; e < 5; ++e) {
-        ci[e] = mine ? __ffs(mine) - 1 : -1;
-        mine &= mine - 1u;
-        v[e] = (own && ci[e] >= 0) ? rowp[ci[e]] : 0.0;
+    for (int e = 0; e < 2; ++e) {
+        const int k = 2 * (bw + 6 * e) + h;
+        if (own && k < nc) {
+            const int cc = col[k];
+            rowp[cc] = fma(-b[cc], vp, a * rowp[cc]);
+        }
     }
-#pragma unroll
-    for (int e = 0; e < 5; ++e)
-        if (own && ci[e] >= 0) rowp[ci[e]] = fma(-b[ci[e]], vp, a * v[e]);
 }
 
 }  // namespace
@@ -277,12 +282,16 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
     __shared__ double ps[2];               // {tau applied to the unscaled data, beta}
     __shared__ double vv[kM];              // helper block: current reflector
     __shared__ double eb[2][kM];           // elimination steps: multipliers b (double buffered)
-    __shared__ double ea[2];               // ... and a
+    __shared__ double ea[2];               // ... a
+    __shared__ double eD[2];               // ... the product of the earlier steps' a
     __shared__ int ep[2];                  // ... pivot column (-1: the row vanished)
-    __shared__ unsigned eact[2];           // ... active columns, pivot included
+    __shared__ int ecol[2][kM];            // ... active columns other than the pivot, in order
+    __shared__ int enc[2];                 // ... their number
+    __shared__ int eng[2];                 // ... G rows taking part (retired pivots and p)
+    __shared__ int eret[kM];               // pivots in the order they were chosen
+    __shared__ double zv[kM];              // z, the direction of the opposite reflector
     __shared__ int s_ew[2];                // biased exponent of max |W| (the B block after Q^)
     __shared__ int s_ez;                   // biased exponent of max |z|
-    __shared__ int s_cs;                   // column of G that holds z
     __shared__ int s_redo;                 // the elimination failed its checks: use the RQ
     __shared__ int s_abort;
 
@@ -523,7 +532,7 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
         }
 
         // pivot and B column segments are final (the B column's block rows are rewritten with
-        // the band); warp 4 stores them while the RQ runs
+        // the band); warp 4 stores them while the elimination runs
         if (warp == 4) {
             for (int i = lane; i < L; i += 32) {
                 A[AT(lda, rlo + i, g.jb)] = col[i];
@@ -534,7 +543,7 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
             if (k + 1 < kl) load_lazy(a, k + 1, nlazy, lvb[(k + 1) & 1], ltb[(k + 1) & 1], grb[(k + 1) & 1], lane, 32);
         }
 
-        // ---- 4. the direction z of the opposite reflector, W z = lambda e_1 (warps 0 .. 3), and
+        // ---- 4. the direction z of the opposite reflector, W z = lambda e_1 (warps 0 .. 3, 5 .. 7), and
         // ---- 5. Z^ from z with the band update.  Attempt 0 finds z by column elimination with
         //      partial pivoting (W M upper triangular up to a column order; z is the column of M
         //      that no step retired): its chain per row is an integer pivot search and one
@@ -551,31 +560,45 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
                     G[i * kLD + cc] = (i == cc) ? 1.0 : 0.0;
                 }
                 __syncthreads();
-                if (tid == 0) {
-                    s_redo = 0;
-                    s_cs = 0;
-                }
-            } else if (tid == 0) {
-                s_cs = 0;
+                if (tid == 0) s_redo = 0;
             }
-            if (gen && m >= 2 && warp < 4) {
+            if (tid == 0 && m < 2) zv[0] = 1.0;   // a 1 x 1 block: z = e_1
+            if (gen && m >= 2 && (attempt == 0 ? warp != 4 : warp < 4)) {
                 if (attempt == 0) {
                     unsigned act = (1u << m) - 1u;   // panel: active columns, current step
-                    int p = -1;
-                    double a = 1.0, b = 0.0;
+                    int p = -1, nret = 0;
+                    double a = 1.0, b = 0.0, D = 1.0;
                     bool bad = false;
+                    // publish step (p, a, b) into slot sl: multipliers, the product D of the
+                    // earlier steps' a, the list of the other active columns, the pivot order
+                    auto publish = [&](int sl) {
+                        if (lane < kM) eb[sl][lane] = b;
+                        if (p >= 0) {
+                            const unsigned cs = act & ~(1u << p);
+                            if (lane < kM && ((cs >> lane) & 1u)) ecol[sl][__popc(cs & ((1u << lane) - 1u))] = lane;
+                        }
+                        if (lane == 0) {
+                            ea[sl] = a;
+                            eD[sl] = D;
+                            ep[sl] = p;
+                            if (p >= 0) {
+                                enc[sl] = __popc(act) - 1;
+                                eret[nret] = p;
+                                eng[sl] = nret + 1;
+                            }
+                            if (bad) s_redo = 1;
+                        }
+                        if (p >= 0) {
+                            ++nret;
+                            D *= a;
+                        }
+                    };
                     if (warp == 0) {
                         const double x = (c < m) ? W[(m - 1) * kLD + c] : 0.0;
                         p = elim_step(x, act, c, &a, &b, &bad);
-                        if (lane < kM) eb[0][lane] = b;
-                        if (lane == 0) {
-                            ea[0] = a;
-                            ep[0] = p;
-                            eact[0] = act;
-                            if (bad) s_redo = 1;
-                        }
+                        publish(0);
                     }
-                    named_barrier(1, 128);
+                    named_barrier(4, 224);
                     for (int t = 0; t + 1 < m; ++t) {
                         const int rho = m - 1 - t, cur = t & 1;
                         if (warp == 0) {
@@ -588,23 +611,24 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
                                     act &= ~(1u << p);
                                 }
                                 p = elim_step(y, act, c, &a, &b, &bad);
-                                if (lane < kM) eb[cur ^ 1][lane] = b;
-                                if (lane == 0) {
-                                    ea[cur ^ 1] = a;
-                                    ep[cur ^ 1] = p;
-                                    eact[cur ^ 1] = act;
-                                    if (bad) s_redo = 1;
-                                }
+                                publish(cur ^ 1);
                             }
                         } else {
-                            // bulk: step t on W rows 0 .. rho-2 and on G
+                            // bulk (warps 1 .. 3, 5 .. 7): step t on W rows 0 .. rho-2 and on G
                             const int pt = ep[cur];
-                            if (pt >= 0) elim_bulk(W, G, eb[cur], ea[cur], pt, eact[cur], rho, m, warp - 1, lane);
+                            if (pt >= 0)
+                                elim_bulk(W, G, eb[cur], ea[cur], eD[cur], pt, ecol[cur], enc[cur], eret, eng[cur], rho,
+                                          warp < 4 ? warp - 1 : warp - 2, lane);
                         }
-                        named_barrier(1, 128);
+                        named_barrier(4, 224);
                     }
-                    // the one column no step retired (the lowest, if rows vanished)
-                    if (warp == 0 && lane == 0) s_cs = __ffs(p >= 0 ? act & ~(1u << p) : act) - 1;
+                    if (warp == 0) {
+                        // z is the one column no step retired (the lowest, if rows vanished); its
+                        // diagonal is the product of all steps' a
+                        const unsigned fin = (p >= 0 && m >= 2) ? act & ~(1u << p) : act;
+                        const int cs = __ffs(fin) - 1;
+                        if (lane < kM) zv[lane] = (lane < m) ? ((lane == cs) ? D : G[lane * kLD + cs]) : 0.0;
+                    }
                 } else {
                     // RQ of the B block with look-ahead
                     double u = 0.0, s1 = 0.0, sc2 = 0.0;   // panel: current reflector
@@ -690,6 +714,7 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
                         }
                         named_barrier(1, 128);
                     }
+                    if (warp == 0 && lane < kM) zv[lane] = (lane < m) ? G[lane * kLD] : 0.0;
                 }
             }
             __syncthreads();
@@ -698,14 +723,13 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
             if (attempt == 0 && tid == 128 && s > 0 && k + 1 < kl) s_abort = !wait_deps(k + 1);
 
             if (gen) {
-                // ---- 5. opposite reflector Z^ from z = G(:, cs) (panel); band dots (warps 5 .. 7)
-                const int cs = s_cs;
+                // ---- 5. opposite reflector Z^ from z (panel); band dots (warps 5 .. 7)
                 double p = 0.0;
                 const bool band = bt >= 0 && bt < nband;
                 const bool isA = bt < na;
                 const int xrow = isA ? x0 + bt : x0 + (bt - na);
                 if (warp == 0) {
-                    const double x = (c < m) ? G[c * kLD + cs] : 0.0;
+                    const double x = (c < m) ? zv[c] : 0.0;
                     double beta, un2;
                     int esc;
                     bool ident;
@@ -737,8 +761,8 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
                     double p0 = 0.0, p1 = 0.0;
 #pragma unroll
                     for (int cc = 0; cc < kM; cc += 2) {
-                        if (cc < m) p0 = fma(brow[cc], G[cc * kLD + cs], p0);
-                        if (cc + 1 < m) p1 = fma(brow[cc + 1], G[(cc + 1) * kLD + cs], p1);
+                        if (cc < m) p0 = fma(brow[cc], zv[cc], p0);
+                        if (cc + 1 < m) p1 = fma(brow[cc + 1], zv[cc + 1], p1);
                     }
                     p = p0 + p1;
                 }
