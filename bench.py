@@ -53,20 +53,19 @@ def paper_flops(n):
 
 def chase_floor_ms(n, r, q, mhz):
     """Latency floor of the chase: the steps on each group's critical path (the last sweep's
-    blocks plus the 3-block lag of each earlier sweep) times the dependent FP64 instructions of
-    one step of the last sweep, 64 cycles each (one FP64 warp instruction occupies its SM
-    sub-partition's FP64 unit for 64 cycles).  Per step (r = 16 kernel): 15 RQ reflectors of
-    18 dependent instructions (one 16-lane reduction that forms u.y and |y|^2 together, the
-    update of the next pivot row, its downdated norm, the square root and the scaled-reflector
-    scalars), 24 each for Q^ and Z^, 18 for the band update and 39 for the last sweep's
-    aggregated lazy updates."""
-    chain = (r - 1) * 18 + 2 * 24 + 18 + 39
+    blocks plus the 3-block lag of each earlier sweep) times the dependent chain of one step of
+    the last sweep.  Per step (r = 16 kernel): r - 1 rows of the pivoted elimination at 332
+    cycles each, the measured latencies of a row's chain on this GPU (a DMUL and a DFMA, 64
+    each; the integer pivot search, 112; a shared load, 29; a shuffle, 37; the barrier, 26),
+    and 105 dependent FP64 instructions of 64 cycles: 24 each for Q^ and Z^, 18 for the band
+    update and 39 for the last sweep's aggregated lazy updates."""
+    chain = (r - 1) * 332 + (2 * 24 + 18 + 39) * 64
     steps = 0
     for j1 in range(1, n - 1, q):
         qg = min(q, n - 2 - j1 + 1)
         jl = j1 + qg - 1
         steps += (2 + (n - jl - 1) // r) + 3 * (qg - 1)
-    return steps * chain * 64 / (mhz * 1e3)
+    return steps * chain / (mhz * 1e3)
 
 
 def sweep_work(n, r):
@@ -258,7 +257,7 @@ def chase_floor(prof, n, r, q, clk, steps):
     floor = chase_floor_ms(n, r, q, mhz)
     ms = prof[name]["ms"] / steps
     return {"kernel": name, "floor_ms": floor, "measured_ms": ms, "frac": floor / ms, "sm_mhz": mhz,
-            "model": "critical-path steps x dependent FP64 instructions per step x 64 cycles"}
+            "model": "critical-path steps x the measured latency of one step's dependent chain"}
 
 
 def run_ours(args, n, r):
