@@ -68,7 +68,11 @@ typedef enum {
  *             bit 30 (HTS_FLAG_TEST_STALL): fault injection for tests of the failure path:
  *             the chase block of the first sweep never publishes its progress, so the next
  *             block's bounded wait (2 s) runs out and HTS_ERR_TIMEOUT is reported by
- *             hts_sync_status; every later kernel of the call then returns at once. */
+ *             hts_sync_status; every later kernel of the call then returns at once.
+ *             bit 29 (HTS_FLAG_TEST_DIRECT_RQ): for tests of the fallback path of the r <= 16
+ *             chase: every step takes the direction of its opposite reflector from the RQ
+ *             of the B block, as when the elimination's residual check fails (the r > 16
+ *             kernel always uses the RQ). */
 typedef struct {
     int q;
     int p;
@@ -80,6 +84,7 @@ typedef struct {
 
 #define HTS_FLAG_NO_CLEAN 1
 #define HTS_FLAG_TEST_STALL (1 << 30)
+#define HTS_FLAG_TEST_DIRECT_RQ (1 << 29)
 
 typedef struct hts_ctx hts_ctx;
 

@@ -31,6 +31,7 @@ HTS_GEMM_EMU_BF16 = 1
 
 HTS_FLAG_NO_CLEAN = 1
 HTS_FLAG_TEST_STALL = 1 << 30
+HTS_FLAG_TEST_DIRECT_RQ = 1 << 29
 
 
 class hts_params(ctypes.Structure):

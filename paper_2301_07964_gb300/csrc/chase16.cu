@@ -563,7 +563,9 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
                 if (tid == 0) s_redo = 0;
             }
             if (tid == 0 && m < 2) zv[0] = 1.0;   // a 1 x 1 block: z = e_1
-            if (gen && m >= 2 && (attempt == 0 ? warp != 4 : warp < 4)) {
+            const bool elim = !a.direct_rq;
+            if (attempt == 0 && !elim && gen && m >= 2 && tid == 0) s_redo = 1;   // tests: RQ only
+            if (gen && m >= 2 && (attempt == 0 ? (elim && warp != 4) : warp < 4)) {
                 if (attempt == 0) {
                     unsigned act = (1u << m) - 1u;   // panel: active columns, current step
                     int p = -1, nret = 0;

@@ -249,6 +249,7 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         ga.epoch = (unsigned long long)(group + 1) << 32;
         ga.status = ctx->d_status;
         ga.stall = (flags & HTS_FLAG_TEST_STALL) ? 1 : 0;
+        ga.direct_rq = (flags & HTS_FLAG_TEST_DIRECT_RQ) ? 1 : 0;
         {
             ProfScope ps(ctx, st);
             e = (r <= 16) ? launch_s2_chase16(ga, st) : launch_s2_generate(ga, st);

@@ -66,7 +66,7 @@ __host__ __device__ __forceinline__ int nblocks_lazy(int n, int r, int j)
 //  i3: last row of A the right reflector touches (Alg. 2); i4: first row of the band that
 //  the generate phase updates.  i4 follows the row-range derivation of the text
 //  (j1 + 1 + max(0, (k + j - j1 - q) r)); Alg. 3 prints a value 2r larger, which leaves
-//  rows of the B block without the preceding right reflector when its RQ is formed.
+//  rows of the B block without the preceding right reflector when its opposite reflector is formed.
 struct StepGeom {
     int jb, i1, i2, i3, i4;
 };
@@ -190,6 +190,7 @@ struct GenArgs {
     unsigned long long epoch;    // (group + 1) << 32
     int *status;
     int stall;                   // fault injection: slot 0 never publishes (tests only)
+    int direct_rq;               // tests: the r <= 16 chase takes every direction from the RQ
 };
 
 // kind 0 = A, 1 = B (Z^ reflectors on rows x < i4(k, j)), 2 = Z (Z^, all rows),

@@ -77,6 +77,26 @@ def test_stage2_matches_oracle(red, oracle_mod, n, r, q):
     assert err <= tol, "max |GPU - oracle| = %.3e > %.3e" % (err, tol)
 
 
+@pytest.mark.parametrize("n,r,q", [(33, 8, 8), (129, 8, 5), (255, 16, 7), (256, 16, 16)])
+def test_rq_fallback_matches_oracle(red, oracle_mod, n, r, q):
+    """The r <= 16 chase finds each opposite reflector's direction by pivoted elimination and
+    falls back to the RQ of the B block when the residual check fails; HTS_FLAG_TEST_DIRECT_RQ
+    takes the fallback in every step, which must meet the same bar."""
+    A, B = random_rht_pencil(n, r, 3000 * n + 10 * r + q)
+    H, T, Q, Z = _gpu_stage2(red, A, B, r, q, flags=b.HTS_FLAG_TEST_DIRECT_RQ)
+    c = rht_pencil_checks(A, B, H, T, Q, Z)
+    assert c["H_below_hessenberg"] == 0.0 and c["T_below_diag"] == 0.0, c
+    for key in ("bwd_A", "bwd_B", "orth_Q", "orth_Z"):
+        assert c[key] < 1e-14 * max(n, 10), c
+    err, tol = _compare(oracle_mod, A, B, r, H, T, Q, Z)
+    assert err <= tol, "max |GPU - oracle| = %.3e > %.3e" % (err, tol)
+    # both paths find the same reduction (the direction is unique up to scale)
+    H2, T2, Q2, Z2 = _gpu_stage2(red, A, B, r, q)
+    g, g2 = canonical(H, T, Q, Z), canonical(H2, T2, Q2, Z2)
+    scale = max(1.0, float(np.abs(A).max()), float(np.abs(B).max()))
+    assert max(float(np.abs(x - y).max()) for x, y in zip(g, g2)) / scale <= 1e-12 * n
+
+
 @pytest.mark.parametrize("n,r,q", [(128, 8, 4), (200, 16, 16)])
 def test_structure_exact_without_final_cleanup(red, n, r, q):
     """The chase annihilates every entry exactly where it reduces it, so the structural
