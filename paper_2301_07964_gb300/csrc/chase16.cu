@@ -270,9 +270,9 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
 {
     __shared__ double col[2 * kMaxR];      // pivot column segment
     __shared__ double bcol[2 * kMaxR];     // newest B column segment
-    __shared__ double W[kM * kLD];         // B block (row-major), then the RQ work array
+    __shared__ double W[kM * kLD];         // B block (row-major), then the elimination's (or RQ's) work array
     __shared__ double Wq[kM * kLD];        // B block after Q^ (band rows i1 .. i2 of B)
-    __shared__ double G[kM * kLD];         // accumulated right factor of the RQ (row-major)
+    __shared__ double G[kM * kLD];         // accumulated column operations (or the RQ's right factor)
     __shared__ double lvb[2][kM * kLD];    // earlier sweeps' left reflectors of block k (buffer k & 1)
     __shared__ double ltb[2][kM];
     __shared__ double grb[2][kM * kM];     // their Gram entries tau_b u_a.u_b, a < b
