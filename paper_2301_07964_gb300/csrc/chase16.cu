@@ -331,9 +331,10 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
         // with the earlier sweeps' ones, which the later sweeps' lazy updates use.
         for (int k = 0; k < kg; ++k) {
             if (tid == 0) {
-                const bool ok = wait_at_least(a.flags + s, a.epoch | (unsigned long long)(k + 1), a.status, a.group, k, j) &&
-                                (s == 0 || wait_at_least(hflags + s - 1, a.epoch | (unsigned long long)(k + 2), a.status,
-                                                         a.group, k, j));
+                const bool ok =
+                    wait_at_least(a.flags + s, a.epoch | (unsigned long long)(k + 1), a.status, a.group, k, j) &&
+                    (s == 0 ||
+                     wait_at_least(hflags + s - 1, a.epoch | (unsigned long long)(k + 2), a.status, a.group, k, j));
                 s_abort = !ok;
             }
             __syncthreads();
