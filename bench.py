@@ -51,21 +51,38 @@ def paper_flops(n):
     return 10.0 * float(n) ** 3
 
 
-def chase_floor_ms(n, r, q, mhz):
-    """Latency floor of the chase: the steps on each group's critical path (the last sweep's
-    blocks plus the 3-block lag of each earlier sweep) times the dependent chain of one step of
-    the last sweep.  Per step (r = 16 kernel): r - 1 rows of the pivoted elimination at 332
-    cycles each, the measured latencies of a row's chain on this GPU (a DMUL and a DFMA, 64
-    each; the integer pivot search, 112; a shared load, 29; a shuffle, 37; the barrier, 26),
-    and 105 dependent FP64 instructions of 64 cycles: 24 each for Q^ and Z^, 18 for the band
-    update and 39 for the last sweep's aggregated lazy updates."""
-    chain = (r - 1) * 332 + (2 * 24 + 18 + 39) * 64
-    steps = 0
+def chase_critical_steps(n, r, q):
+    """Steps on the chase's critical path, summed over the groups, under the kernel's waits:
+    step (k, j) follows step (k-1, j), and sweep j-1's block k+2 (or its last block).  With
+    unit steps, fin_j(k) = k + 1 + max_{i <= k} (fin_{j-1}(min(i+2, K_{j-1}-1)) - i), where
+    K_j = 2 + (n-j-1) // r are the blocks sweep j walks (Alg. 3)."""
+    total = 0
     for j1 in range(1, n - 1, q):
         qg = min(q, n - 2 - j1 + 1)
-        jl = j1 + qg - 1
-        steps += (2 + (n - jl - 1) // r) + 3 * (qg - 1)
-    return steps * chain / (mhz * 1e3)
+        prev = None
+        for s in range(qg):
+            K = 2 + (n - (j1 + s) - 1) // r
+            k = np.arange(K)
+            if prev is None:
+                fin = k + 1
+            else:
+                dep = prev[np.minimum(k + 2, len(prev) - 1)]
+                fin = k + 1 + np.maximum.accumulate(dep - k)
+            prev = fin
+        total += int(prev[-1])
+    return total
+
+
+def chase_floor_ms(n, r, q, mhz):
+    """Latency floor of the chase: the steps on each group's critical path
+    (chase_critical_steps) times the dependent chain of one step.  Per step (r = 16 kernel):
+    r - 1 rows of the pivoted elimination at 332 cycles each, the measured latencies of a
+    row's chain on this GPU (a DMUL and a DFMA, 64 each; the integer pivot search, 112; a
+    shared load, 29; a shuffle, 37; the barrier, 26), and 105 dependent FP64 instructions of
+    64 cycles: 24 each for Q^ and Z^, 18 for the band update and 39 for the last sweep's
+    aggregated lazy updates."""
+    chain = (r - 1) * 332 + (2 * 24 + 18 + 39) * 64
+    return chase_critical_steps(n, r, q) * chain / (mhz * 1e3)
 
 
 def sweep_work(n, r):
