@@ -121,7 +121,11 @@ hts_status hts_reduce_stage1(hts_ctx *ctx, int n, int r,
  * generate / apply schedule this implementation runs).  Requires 1 <= r and n >= 1; entries
  * of A below the r-th subdiagonal and of B below the diagonal are treated as zero.  r = 1
  * (and n <= 2) is a no-op apart from HTS_COMP_INIT.  Reflectors act on rows/columns 2..n
- * only, so Q e_1 and Z e_1 are unchanged.
+ * only, so Q e_1 and Z e_1 are unchanged.  Each step's opposite reflector is the one the paper
+ * forms from an RQ of the B block; its first column is the direction z with (B block) z
+ * parallel to e_1.  For r <= 16 the library finds z by column elimination with partial
+ * pivoting and checks the entries the reflector zeroes against 2^-44 max|block| max|z|; a
+ * step that fails the check (or meets extreme magnitudes) takes z from the RQ.
  * mode selects the arithmetic of the delayed updates (Alg. 4): HTS_GEMM_FP64 applies the
  * reflectors one at a time in native FP64; HTS_GEMM_EMU_BF16 forms each block's reflector
  * product U_k (w x w, w = r + q - 1) and applies it as a product emulated on the BF16 tensor
