@@ -15,8 +15,15 @@
  *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy
  *    default stream).  Argument errors are detected on the host before anything is
  *    enqueued and are returned as HTS_ERR_ARG / HTS_ERR_WORKSPACE / HTS_ERR_UNSUPPORTED.
- *    Errors found on the device (a bounded inter-block wait that ran out) are recorded in a
- *    status word of the context and reported by hts_sync_status().
+ *    Errors found on the device are recorded in a status word of the context and reported by
+ *    hts_sync_status(): a bounded inter-block wait that ran out (HTS_ERR_TIMEOUT), and a NaN or
+ *    infinite entry among the inputs a call reads (HTS_ERR_NONFINITE, info = {0, matrix (0 A,
+ *    1 B, 2 Q, 3 Z), row, column}; for the batched call {pencil, matrix, row, column}).  Every
+ *    call first scans the entries it reads: A on and above its r-th subdiagonal and the upper
+ *    triangle of B for stage 2, all of A and the upper triangle of B for stage 1, all of A and
+ *    B for the full reduction, and Q / Z with HTS_COMP_UPDATE.  After a non-finite input the
+ *    stage-2 kernels do nothing; stages 0 and 1 of the full reduction may still run, so the
+ *    contents of the matrices are then unspecified.
  *  - On exit A holds H and B holds T with exact zeros below the first subdiagonal of H and
  *    below the diagonal of T.
  *  - compq / compz: HTS_COMP_NONE leaves Q / Z untouched (the pointer may be NULL);
@@ -39,7 +46,7 @@ typedef enum {
     HTS_ERR_CUDA = 2,         /* a CUDA runtime call failed (launch, stream, device) */
     HTS_ERR_WORKSPACE = 3,    /* work is NULL, misaligned or smaller than required */
     HTS_ERR_TIMEOUT = 4,      /* a bounded wait between thread blocks ran out (device) */
-    HTS_ERR_NONFINITE = 5,    /* reserved: NaN / Inf input */
+    HTS_ERR_NONFINITE = 5,    /* NaN / Inf among the input entries (device; hts_sync_status) */
     HTS_ERR_UNSUPPORTED = 6   /* valid request this build does not implement */
 } hts_status;
 
@@ -148,9 +155,11 @@ hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r,
  * The paper has no counterpart: this is a deployment variant of hts_reduce_stage2 with the
  * same arguments minus work / work_bytes and the same results.
  *  - Scratch lives in one fixed 8 MiB array compiled into the library; every GPU that loads
- *    the library holds it until the process exits.  Sizes whose workspace
- *    (hts_workspace_size) exceeds 8 MiB are rejected with HTS_ERR_WORKSPACE before anything
- *    runs (native mode: r = 16 allows n up to about 10400, r = 32 up to about 7900).
+ *    the library holds it until the process exits.  A call whose stage-2 scratch in the chosen
+ *    update mode exceeds 8 MiB is rejected with HTS_ERR_WORKSPACE before anything runs (the
+ *    check precedes every other argument check).  In native FP64 mode r = 16 fits n up to
+ *    about 9000; the emulated mode's digit planes (64 KiB per block of r columns) fit only
+ *    small n (about 500 at r = 16).
  *  - The call allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  *    with that device current); make that first call before any stream capture.

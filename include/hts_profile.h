@@ -48,6 +48,13 @@ hts_status hts_profile_begin(hts_ctx *ctx, int max_launches);
  * number of launches that did not fit into the pool. */
 hts_status hts_profile_end(hts_ctx *ctx, hts_kernel_profile out[HTS_K_NKINDS], int *dropped);
 
+/* Number of chase steps (r <= 16) whose opposite-reflector direction failed the checks of the
+ * column elimination (residual above 2^-44 max|block| max|z|, or a pivot outside 2^+-960) and
+ * was recomputed from the RQ of the B block, counted on the device since the context was
+ * created or since the previous call of this function.  Waits for `stream` first.  Steps forced
+ * onto the RQ by HTS_FLAG_TEST_DIRECT_RQ are not counted. */
+hts_status hts_fallback_count(hts_ctx *ctx, void *stream, long long *count);
+
 /* Measure the FP64 fused multiply-add throughput of the current device (TFLOP/s, 2 flops per
  * FMA) with a short kernel on `stream`; blocks until it finishes. */
 hts_status hts_probe_fp64_peak(void *stream, double *tflops);

@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
     lib.hts_profile_end.restype = _I
     lib.hts_probe_fp64_peak.argtypes = [_VP, ctypes.POINTER(ctypes.c_double)]
     lib.hts_probe_fp64_peak.restype = _I
+    lib.hts_fallback_count.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_longlong)]
+    lib.hts_fallback_count.restype = _I
     _lib = lib
     return lib
 
@@ -258,4 +260,14 @@ def hts_probe_fp64_peak(stream=None) -> float:
     st = load().hts_probe_fp64_peak(_stream(stream), ctypes.byref(v))
     if st != HTS_OK:
         raise HTSError(st, "hts_probe_fp64_peak")
+    return v.value
+
+
+def hts_fallback_count(ctx, stream=None) -> int:
+    """Chase steps whose elimination-based opposite reflector was redone with the RQ since the
+    previous query (waits for the stream)."""
+    v = ctypes.c_longlong(0)
+    st = load().hts_fallback_count(ctx, _stream(stream), ctypes.byref(v))
+    if st != HTS_OK:
+        raise HTSError(st, "hts_fallback_count")
     return v.value

@@ -39,19 +39,55 @@ __device__ __forceinline__ double bsum(double x, BatchShared &S)
     return s;
 }
 
-// Reflector (dlarfg convention) from m entries x[0], x[inc], ...; v goes to S.v (v_0 = 1),
-// tau / beta to S.tau / S.beta; x is overwritten by (beta, 0, ..., 0).
-__device__ void blk_larfg(double *x, long inc, int m, BatchShared &S)
+__device__ __forceinline__ double bmax(double x, BatchShared &S)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    x = warp_max(x);
+    __syncthreads();
+    if (lane == 0) S.red[warp] = x;
+    __syncthreads();
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kBW; ++w) s = fmax(s, S.red[w]);
+    return s;
+}
+
+// Householder data (dlarfg convention) of the vector with pivot alpha and other entries
+// get(0 .. cnt-1): S.tau, S.beta, and S.scale, the factor that turns an entry into its
+// component of v (v_pivot = 1).  The sum of squares is formed directly and, when it leaves
+// [1e-290, 1e290] or alpha exceeds 1e145, again with every entry divided by the largest
+// magnitude, so that no intermediate over- or underflows.  tau = 0 (the identity) only when
+// every other entry is exactly zero.  Called by the whole block.
+template <class Get>
+__device__ void blk_house(double alpha, int cnt, Get get, BatchShared &S)
 {
     double part = 0.0;
-    for (int i = 1 + threadIdx.x; i < m; i += kBT) part += x[i * inc] * x[i * inc];
-    const double ssq = bsum(part, S);
+    for (int i = threadIdx.x; i < cnt; i += kBT) part = fma(get(i), get(i), part);
+    double ssq = bsum(part, S);
+    double scale = 1.0;
+    if (!(ssq >= 1e-290 && ssq <= 1e290) || fabs(alpha) > 1e145) {   // uniform over the block
+        double mp = 0.0;
+        for (int i = threadIdx.x; i < cnt; i += kBT) mp = fmax(mp, fabs(get(i)));
+        const double mx = bmax(mp, S);
+        if (mx == 0.0) {
+            ssq = 0.0;
+        } else {
+            scale = fmax(mx, fabs(alpha));
+            const double rs = 1.0 / scale;
+            part = 0.0;
+            for (int i = threadIdx.x; i < cnt; i += kBT) {
+                const double t = get(i) * rs;
+                part = fma(t, t, part);
+            }
+            ssq = bsum(part, S);
+        }
+    }
     if (threadIdx.x == 0) {
-        const double alpha = x[0];
-        if (m <= 1 || ssq == 0.0) {
+        if (cnt <= 0 || ssq == 0.0) {
             S.tau = 0.0; S.beta = alpha; S.scale = 0.0;
         } else {
-            const double nrm = sqrt(alpha * alpha + ssq);
+            const double as = alpha / scale;
+            const double nrm = scale * sqrt(fma(as, as, ssq));
             const double b = alpha >= 0.0 ? -nrm : nrm;
             S.tau = (b - alpha) / b;
             S.scale = 1.0 / (alpha - b);
@@ -59,6 +95,13 @@ __device__ void blk_larfg(double *x, long inc, int m, BatchShared &S)
         }
     }
     __syncthreads();
+}
+
+// Reflector (dlarfg convention) from m entries x[0], x[inc], ...; v goes to S.v (v_0 = 1),
+// tau / beta to S.tau / S.beta; x is overwritten by (beta, 0, ..., 0).
+__device__ void blk_larfg(double *x, long inc, int m, BatchShared &S)
+{
+    blk_house(x[0], m - 1, [&](int i) { return x[(i + 1) * inc]; }, S);
     for (int i = threadIdx.x; i < m; i += kBT) {
         S.v[i] = (i == 0) ? 1.0 : x[i * inc] * S.scale;
         x[i * inc] = (i == 0) ? S.beta : 0.0;
@@ -107,20 +150,9 @@ __device__ void blk_rq_first_rows(int m, int l, BatchShared &S)
     const int ldw = m + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int s = m - 1; s >= 1; --s) {
-        double part = 0.0;
-        for (int c = threadIdx.x; c < s; c += kBT) part += S.W[s * ldw + c] * S.W[s * ldw + c];
-        const double ssq = bsum(part, S);
-        if (threadIdx.x == 0) {
-            const double alpha = S.W[s * ldw + s];
-            if (ssq == 0.0) {
-                S.tau = 0.0; S.beta = alpha; S.scale = 0.0;
-            } else {
-                const double nrm = sqrt(alpha * alpha + ssq);
-                const double b = alpha >= 0.0 ? -nrm : nrm;
-                S.tau = (b - alpha) / b; S.scale = 1.0 / (alpha - b); S.beta = b;
-            }
-            S.rqt[s] = S.tau;
-        }
+        const double *wrow = &S.W[s * ldw];
+        blk_house(wrow[s], s, [&](int c) { return wrow[c]; }, S);
+        if (threadIdx.x == 0) S.rqt[s] = S.tau;
         __syncthreads();
         for (int c = threadIdx.x; c < s; c += kBT) S.W[s * ldw + c] *= S.scale;
         __syncthreads();
@@ -168,14 +200,33 @@ struct BatchDesc {
 };
 
 __global__ void __launch_bounds__(kBT) k_reduce_batched(const BatchDesc *desc, const int *order, int p_param,
-                                                         int compq, int compz, const int *status)
+                                                         int compq, int compz, int *status)
 {
     __shared__ BatchShared S;
     const BatchDesc d = desc[order[blockIdx.x]];
     const int n = d.n, r = d.r;
     double *A = d.A, *B = d.B;
     double *Q = compq ? d.Q : nullptr, *Z = compz ? d.Z : nullptr;
-    if (__ldcg(status) != 0) return;
+    // NaN / Inf among the pencil's inputs: record it (the first one of the batch is reported)
+    // and leave this pencil alone; the other pencils are reduced
+    {
+        int bad = 0;
+        for (int e = threadIdx.x; e < n * n && !bad; e += kBT) {
+            const int i = e % n + 1, c = e / n + 1;
+            const int which = (((__double_as_longlong(A[AT(d.lda, i, c)]) >> 52) & 0x7ff) == 0x7ff) ? 1
+                              : (((__double_as_longlong(B[AT(d.ldb, i, c)]) >> 52) & 0x7ff) == 0x7ff) ? 2
+                              : (compq == HTS_COMP_UPDATE &&
+                                 ((__double_as_longlong(Q[AT(d.ldq, i, c)]) >> 52) & 0x7ff) == 0x7ff) ? 3
+                              : (compz == HTS_COMP_UPDATE &&
+                                 ((__double_as_longlong(Z[AT(d.ldz, i, c)]) >> 52) & 0x7ff) == 0x7ff) ? 4
+                                                                                                  : 0;
+            if (which) {
+                record_error(status, HTS_ERR_NONFINITE, order[blockIdx.x], which - 1, i, c);
+                bad = 1;
+            }
+        }
+        if (__syncthreads_or(bad)) return;
+    }
     // identity initialisation
     for (int e = threadIdx.x; e < n * n; e += kBT) {
         const int i = e % n + 1, c = e / n + 1;
@@ -273,7 +324,7 @@ __global__ void __launch_bounds__(kBT) k_reduce_batched(const BatchDesc *desc, c
 }
 
 cudaError_t launch_reduce_batched(const void *desc, const int *order, int count, int p, int compq, int compz,
-                                  const int *status, cudaStream_t st)
+                                  int *status, cudaStream_t st)
 {
     k_reduce_batched<<<count, kBT, 0, st>>>(static_cast<const BatchDesc *>(desc), order, p, compq, compz, status);
     return cudaGetLastError();

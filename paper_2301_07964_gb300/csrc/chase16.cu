@@ -794,6 +794,8 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
                 }
             }
             __syncthreads();
+            // count the steps whose elimination failed its checks (status word slot 5)
+            if (attempt == 0 && s_redo && !a.direct_rq && tid == 0) atomicAdd(a.status + kStatusFallbacks, 1);
             if (!s_redo) break;
         }
 

@@ -88,6 +88,21 @@ hts_status check_common(hts_ctx *ctx, int n, int r, const double *A, int lda, co
 
 hts_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HTS_OK : HTS_ERR_CUDA; }
 
+// Scan of the entries a call reads for NaN / Inf (reported as HTS_ERR_NONFINITE by
+// hts_sync_status): A on and above its lowA-th subdiagonal, B on and above its lowB-th, and Q,
+// Z where the call multiplies into them (HTS_COMP_UPDATE).
+hts_status scan_inputs(hts_ctx *ctx, int n, const double *A, int lda, int lowA, const double *B, int ldb, int lowB,
+                       hts_comp compq, const double *Q, int ldq, hts_comp compz, const double *Z, int ldz,
+                       cudaStream_t st)
+{
+    int *s = ctx->d_status;
+    if (launch_scan_nonfinite(A, lda, n, lowA, 0, s, st) != cudaSuccess) return HTS_ERR_CUDA;
+    if (launch_scan_nonfinite(B, ldb, n, lowB, 1, s, st) != cudaSuccess) return HTS_ERR_CUDA;
+    if (compq == HTS_COMP_UPDATE && launch_scan_nonfinite(Q, ldq, n, n, 2, s, st) != cudaSuccess) return HTS_ERR_CUDA;
+    if (compz == HTS_COMP_UPDATE && launch_scan_nonfinite(Z, ldz, n, n, 3, s, st) != cudaSuccess) return HTS_ERR_CUDA;
+    return HTS_OK;
+}
+
 // The emulated updates keep one window of r + q - 1 <= 32 indices in the registers of a warp
 // and slide it by one 16-wide operand tile per block: r = 16 only, with 8 digits per operand.
 hts_status check_emu(hts_gemm_mode mode, int r, int q, const hts_params *p)
@@ -205,6 +220,9 @@ GroupCost s2_group_cost(int n, int r, int j1, int qg, bool hasQ, bool hasZ, bool
 // Bytes of caller scratch stage 2 alone needs in native FP64 mode (two reflector sets and
 // the progress words).
 size_t stage2_workspace_bytes(int n, int r) { return s2_layout(n, r).total_fp64; }
+
+// ... and in the given update mode (the emulated mode adds the digit planes).
+size_t stage2_workspace_bytes_mode(int n, int r, hts_gemm_mode mode) { return s2_bytes(n, r, mode); }
 
 // Stage 2 driver: the group loop of generate / apply launches.
 hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B, int ldb,
@@ -344,8 +362,8 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         return HTS_ERR_CUDA;
     if (!(flags & HTS_FLAG_NO_CLEAN)) {
         ProfScope ps(ctx, st);
-        if ((e = launch_zero_below(A, lda, n, 1, st)) != cudaSuccess) return HTS_ERR_CUDA;
-        if ((e = launch_zero_below(B, ldb, n, 0, st)) != cudaSuccess) return HTS_ERR_CUDA;
+        if ((e = launch_zero_below(A, lda, n, 1, ctx->d_status, st)) != cudaSuccess) return HTS_ERR_CUDA;
+        if ((e = launch_zero_below(B, ldb, n, 0, ctx->d_status, st)) != cudaSuccess) return HTS_ERR_CUDA;
         ps.done(HTS_K_UTIL, 0.0, 0.0);
     }
     return HTS_OK;
@@ -449,6 +467,11 @@ hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, dou
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     double *Qp = compq == HTS_COMP_NONE ? nullptr : Q;
     double *Zp = compz == HTS_COMP_NONE ? nullptr : Z;
+    {
+        ProfScope ps(ctx, st);
+        if ((s = scan_inputs(ctx, n, A, lda, r, B, ldb, 0, compq, Q, ldq, compz, Z, ldz, st)) != HTS_OK) return s;
+        ps.done(HTS_K_UTIL, 0.0, 0.0);
+    }
     if (compq == HTS_COMP_INIT || compz == HTS_COMP_INIT) {
         ProfScope ps(ctx, st);
         if (compq == HTS_COMP_INIT && (s = cuda_status(launch_set_identity(Q, ldq, n, st))) != HTS_OK) return s;
@@ -487,9 +510,10 @@ hts_status hts_reduce_stage1(hts_ctx *ctx, int n, int r, double *A, int lda, dou
     double *Qp = compq == HTS_COMP_NONE ? nullptr : Q;
     double *Zp = compz == HTS_COMP_NONE ? nullptr : Z;
     ProfScope ps(ctx, st);
+    if ((s = scan_inputs(ctx, n, A, lda, n, B, ldb, 0, compq, Q, ldq, compz, Z, ldz, st)) != HTS_OK) return s;
     if (compq == HTS_COMP_INIT && launch_set_identity(Q, ldq, n, st) != cudaSuccess) return HTS_ERR_CUDA;
     if (compz == HTS_COMP_INIT && launch_set_identity(Z, ldz, n, st) != cudaSuccess) return HTS_ERR_CUDA;
-    if (launch_zero_below(B, ldb, n, 0, st) != cudaSuccess) return HTS_ERR_CUDA;
+    if (launch_zero_below(B, ldb, n, 0, ctx->d_status, st) != cudaSuccess) return HTS_ERR_CUDA;
     if (run_stage1(n, r, stage1_p(p, r), A, lda, B, ldb, Qp, ldq, Zp, ldz, work, st) != cudaSuccess)
         return HTS_ERR_CUDA;
     ps.done(HTS_K_STAGE1, 0.0, 0.0);
@@ -510,6 +534,7 @@ hts_status hts_reduce(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         DeviceGuard g(ctx->device);
         if (!g.ok) return HTS_ERR_CUDA;
         cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if ((s = scan_inputs(ctx, n, A, lda, n, B, ldb, n, compq, Q, ldq, compz, Z, ldz, st)) != HTS_OK) return s;
         if (compq == HTS_COMP_INIT && launch_set_identity(Q, ldq, n, st) != cudaSuccess) return HTS_ERR_CUDA;
         if (compz == HTS_COMP_INIT && launch_set_identity(Z, ldz, n, st) != cudaSuccess) return HTS_ERR_CUDA;
         if (run_stage0(n, A, lda, B, ldb, compq == HTS_COMP_NONE ? nullptr : Q, ldq, work, r, stage1_p(p, r),
@@ -529,6 +554,7 @@ hts_status hts_reduce(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
     double *Zp = compz == HTS_COMP_NONE ? nullptr : Z;
     {
         ProfScope ps(ctx, st);
+        if ((s = scan_inputs(ctx, n, A, lda, n, B, ldb, n, compq, Q, ldq, compz, Z, ldz, st)) != HTS_OK) return s;
         if (compq == HTS_COMP_INIT && launch_set_identity(Q, ldq, n, st) != cudaSuccess) return HTS_ERR_CUDA;
         if (compz == HTS_COMP_INIT && launch_set_identity(Z, ldz, n, st) != cudaSuccess) return HTS_ERR_CUDA;
         if (run_stage0(n, A, lda, B, ldb, Qp, ldq, work, r, stage1_p(p, r), st) != cudaSuccess) return HTS_ERR_CUDA;
@@ -605,6 +631,20 @@ hts_status hts_reduce_batched(hts_ctx *ctx, int count, const int *n, const int *
     return HTS_OK;
 }
 
+hts_status hts_fallback_count(hts_ctx *ctx, void *stream, long long *count)
+{
+    if (!ctx || !count) return HTS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return HTS_ERR_CUDA;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return HTS_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, ctx->d_status + kStatusFallbacks, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(ctx->d_status + kStatusFallbacks, 0, sizeof(int)) != cudaSuccess)
+        return HTS_ERR_CUDA;
+    *count = v;
+    return HTS_OK;
+}
+
 hts_status hts_sync_status(hts_ctx *ctx, void *stream, int info[4])
 {
     if (!ctx) return HTS_ERR_ARG;
@@ -614,7 +654,7 @@ hts_status hts_sync_status(hts_ctx *ctx, void *stream, int info[4])
     if (cudaStreamSynchronize(st) != cudaSuccess) return HTS_ERR_CUDA;
     if (cudaMemcpy(ctx->h_status, ctx->d_status, kStatusWords * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return HTS_ERR_CUDA;
-    if (cudaMemset(ctx->d_status, 0, kStatusWords * sizeof(int)) != cudaSuccess) return HTS_ERR_CUDA;
+    if (cudaMemset(ctx->d_status, 0, kStatusFallbacks * sizeof(int)) != cudaSuccess) return HTS_ERR_CUDA;
     if (info)
         for (int i = 0; i < 4; ++i) info[i] = ctx->h_status[1 + i];
     return static_cast<hts_status>(ctx->h_status[0]);

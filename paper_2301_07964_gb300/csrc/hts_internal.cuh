@@ -34,6 +34,7 @@ struct hts_ctx {
 namespace hts {
 
 constexpr int kStatusWords = 8;
+constexpr int kStatusFallbacks = 5;  // status word slot: opposite-reflector steps redone with the RQ
 constexpr int kMaxR = 32;            // reflector length limit of the warp-level chase
 constexpr int kGenThreads = 256;     // threads of one generate (chase) block
 constexpr int kApplyThreads = 64;    // threads (rows or columns) of one apply block
@@ -244,12 +245,13 @@ bool emu_supported(int r, int qg);
 cudaError_t launch_s2_apply_right(const ApplyArgs &a, int nmat, cudaStream_t st);
 cudaError_t launch_s2_apply_left(const LeftArgs &a, cudaStream_t st);
 cudaError_t launch_set_identity(double *M, int ld, int n, cudaStream_t st);
-cudaError_t launch_zero_below(double *M, int ld, int n, int band, cudaStream_t st);
+cudaError_t launch_zero_below(double *M, int ld, int n, int band, const int *status, cudaStream_t st);
+cudaError_t launch_scan_nonfinite(const double *M, int ld, int n, int lower, int which, int *status, cudaStream_t st);
 
 // Batched reduction (batch.cu).
 struct BatchDesc;
 cudaError_t launch_reduce_batched(const void *desc, const int *order, int count, int p, int compq, int compz,
-                                  const int *status, cudaStream_t st);
+                                  int *status, cudaStream_t st);
 size_t batch_desc_bytes();
 void fill_batch_desc(void *dst, int i, double *A, double *B, double *Q, double *Z, int n, int r, int lda, int ldb,
                      int ldq, int ldz);
@@ -259,6 +261,7 @@ int batch_max_block();
 // Stages 0 and 1 (stage01.cu) and workspace sizes.
 size_t stage01_workspace_bytes(int n, int r, int p);
 size_t stage2_workspace_bytes(int n, int r);
+size_t stage2_workspace_bytes_mode(int n, int r, hts_gemm_mode mode);
 cudaError_t run_stage0(int n, double *A, int lda, double *B, int ldb, double *Q, int ldq, void *work, int r, int p,
                        cudaStream_t st);
 cudaError_t run_stage1(int n, int nb, int p, double *A, int lda, double *B, int ldb, double *Q, int ldq,

@@ -59,7 +59,7 @@ extern "C" hts_status hts_reduce_stage2_noalloc(hts_ctx *ctx, int n, int r,
     size_t need = 0;
     const hts_status s = hts_workspace_size(n, r, p, &need);   // validates n and r
     if (s != HTS_OK) return s;
-    need = hts::stage2_workspace_bytes(n, r);                   // stage 2 alone runs here
+    need = hts::stage2_workspace_bytes_mode(n, r, mode);        // stage 2 alone runs here
     if (need > kNoAllocScratchBytes) return HTS_ERR_WORKSPACE;
     void *scratch = nullptr;
     const hts_status a = scratch_address(ctx->device, &scratch);

@@ -146,12 +146,27 @@ __global__ void k_set_identity(double *M, int ld, int n)
         M[AT(ld, i, c)] = (i == c) ? 1.0 : 0.0;
 }
 
-// Zero A below its first subdiagonal (band = 1) or B below its diagonal (band = 0).
-__global__ void k_zero_below(double *M, int ld, int n, int band)
+// Zero A below its first subdiagonal (band = 1) or B below its diagonal (band = 0); skipped
+// once an earlier kernel of the call has recorded an error.
+__global__ void k_zero_below(double *M, int ld, int n, int band, const int *status)
 {
+    if (__ldcg(status) != 0) return;
     const int c = blockIdx.y + 1;
     for (int i = c + band + 1 + blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
         M[AT(ld, i, c)] = 0.0;
+}
+
+// Entries a call reads that are NaN or infinite (exponent field all ones): column c, rows 1 ..
+// min(n, c + lower).  The first one found is recorded as HTS_ERR_NONFINITE with {0, which, row,
+// column}; every kernel of the reduction that checks the status word then does nothing.
+__global__ void k_scan_nonfinite(const double *M, int ld, int n, int lower, int which, int *status)
+{
+    const int c = blockIdx.y + 1;
+    const int last = imin(n, c + lower);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x + 1; i <= last; i += gridDim.x * blockDim.x) {
+        const long long bits = __double_as_longlong(__ldg(M + AT(ld, i, c)));
+        if (((bits >> 52) & 0x7ff) == 0x7ff) record_error(status, HTS_ERR_NONFINITE, 0, which, i, c);
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -207,11 +222,19 @@ cudaError_t launch_set_identity(double *M, int ld, int n, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_zero_below(double *M, int ld, int n, int band, cudaStream_t st)
+cudaError_t launch_zero_below(double *M, int ld, int n, int band, const int *status, cudaStream_t st)
 {
     if (n <= band + 1) return cudaSuccess;
     dim3 grid((n + 255) / 256, n);
-    k_zero_below<<<grid, 256, 0, st>>>(M, ld, n, band);
+    k_zero_below<<<grid, 256, 0, st>>>(M, ld, n, band, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_nonfinite(const double *M, int ld, int n, int lower, int which, int *status, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    dim3 grid((n + 255) / 256, n);
+    k_scan_nonfinite<<<grid, 256, 0, st>>>(M, ld, n, lower, which, status);
     return cudaGetLastError();
 }
 

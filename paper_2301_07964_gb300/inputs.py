@@ -12,6 +12,12 @@ The paper measures on random pencils whose B is QR-factorised first (Section
 * ``random_rht_pencil``      an r-Hessenberg-triangular pencil: A iid N(0, 1) on and above
                              the r-th subdiagonal, zero below; B = the R factor of an iid
                              N(0, 1) matrix (the distribution stage 0 hands to stage 1)
+* ``ill_conditioned_rht_pencil``  the r-HT pencil of the same family: A iid N(0, 1) on and
+                             above the r-th subdiagonal, B = the R factor of
+                             U diag(10^(-e i/(n-1))) V^T (condition number 10^e)
+* ``saddle_point_pencil``    (A, B) = ([[X, Y], [Y^T, 0]], diag(I_m, 0)) with X = G G^T / m + I
+                             symmetric positive definite, Y iid N(0, 1) and m = n - n // 8, so
+                             that a quarter of the eigenvalues (2 (n - m)) are infinite
 * ``batch_sizes``            pencil sizes n_i ~ U{32..512} with r_i = min(8, n_i // 8)
 
 All arrays are float64 in Fortran (column-major) order.
@@ -63,6 +69,36 @@ def random_rht_pencil(n: int, r: int, seed: int):
     B = np.linalg.qr(X, mode="r")
     B = np.asfortranarray(np.triu(B))
     return A, B
+
+
+def ill_conditioned_rht_pencil(n: int, r: int, seed: int, decades: float = 8.0):
+    """r-HT pencil with an ill-conditioned triangular B: A(i, j) iid N(0, 1) for i <= j + r
+    (zero below), B = R of the QR factorisation of U diag(logspace(0, -decades, n)) V^T."""
+    g = _rng(seed)
+    A = np.asfortranarray(np.triu(g.standard_normal((n, n)), -r))
+    U = haar_orthogonal(n, g)
+    V = haar_orthogonal(n, g)
+    s = 10.0 ** (-decades * np.arange(n) / max(n - 1, 1))
+    B = np.linalg.qr((U * s[None, :]) @ V.T, mode="r")
+    return A, np.asfortranarray(np.triu(B))
+
+
+def saddle_point_pencil(n: int, seed: int):
+    """Saddle-point pencil of the paper's experiment: A = [[X, Y], [Y^T, 0]] with X symmetric
+    positive definite (X = G G^T / m + I) and Y iid N(0, 1); B = diag(I_m, 0) with
+    m = n - n // 8, so that 2 (n - m) = n / 4 eigenvalues are infinite."""
+    g = _rng(seed)
+    m = n - n // 8
+    G = g.standard_normal((m, m))
+    X = G @ G.T / m + np.eye(m)
+    Y = g.standard_normal((m, n - m))
+    A = np.zeros((n, n))
+    A[:m, :m] = X
+    A[:m, m:] = Y
+    A[m:, :m] = Y.T
+    B = np.zeros((n, n))
+    B[np.arange(m), np.arange(m)] = 1.0
+    return np.asfortranarray(A), np.asfortranarray(B)
 
 
 def batch_sizes(count: int, seed: int, lo: int = 32, hi: int = 512):

@@ -1,0 +1,225 @@
+"""Robustness of the GPU path through the C ABI.
+
+* Non-finite inputs: a NaN or an infinity among the entries a call reads is reported by
+  hts_sync_status as HTS_ERR_NONFINITE with its matrix, row and column; stage 2 then leaves
+  the pencil untouched, and the context serves the next call.  Entries a call does not read
+  (below the band of an r-HT pencil) are ignored.  In a batch, the pencil with the bad entry
+  is reported and skipped, and the others are reduced.
+* The ill-conditioned B of the paper's experiments (B = U diag(logspace(0, -8)) V^T, condition
+  number 1e8) at r = 8, 16 (the chase's elimination path, and its RQ fallback forced for every
+  step) and 32 (the RQ chase): the HT form is compared with the oracle's element by element in
+  canonical signs (1e-12 n relative), besides the invariants.  The count of steps whose
+  elimination failed its residual check and was redone with the RQ is reported.
+* The saddle-point pencils of the paper's experiment (a quarter of the eigenvalues infinite,
+  T singular): invariants only, since the HT form is not unique when T is singular.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from hts_checks import canonical, rht_pencil_checks  # noqa: E402
+from paper_2301_07964_gb300 import binding as b  # noqa: E402
+from paper_2301_07964_gb300.inputs import (ill_conditioned_pencil, ill_conditioned_rht_pencil,  # noqa: E402
+                                           random_pencil, random_rht_pencil, saddle_point_pencil)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def red():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2301_07964_gb300 import build
+    build.build()
+    from paper_2301_07964_gb300.device import Reducer
+    r = Reducer(0)
+    yield r
+    r.close()
+
+
+def _dev(*Ms):
+    from paper_2301_07964_gb300.device import to_device
+    return [to_device(M) for M in Ms]
+
+
+def _host(*ts):
+    from paper_2301_07964_gb300.device import to_host
+    return [to_host(t) for t in ts]
+
+
+def _empty(n):
+    from paper_2301_07964_gb300.device import colmajor_empty
+    return colmajor_empty(n)
+
+
+def _check_invariants(A, B, H, T, Q, Z, tol):
+    c = rht_pencil_checks(A, B, H, T, Q, Z)
+    assert c["H_below_hessenberg"] == 0.0 and c["T_below_diag"] == 0.0, c
+    for key in ("bwd_A", "bwd_B", "orth_Q", "orth_Z"):
+        assert c[key] < tol, c
+    return c
+
+
+# ---------------------------------------------------------------------------------------
+# non-finite inputs
+# ---------------------------------------------------------------------------------------
+
+def test_nonfinite_stage2_reported_and_pencil_untouched(red):
+    n, r = 64, 8
+    A, B = random_rht_pencil(n, r, 5)
+    for which, (i, j), val in ((0, (10, 5), np.nan), (1, (3, 20), np.inf), (1, (0, 63), -np.inf)):
+        A2, B2 = A.copy(), B.copy()
+        (A2 if which == 0 else B2)[i, j] = val
+        dA, dB = _dev(A2, B2)
+        dQ, dZ = _empty(n), _empty(n)
+        red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=4)
+        st, info = red.sync_status()
+        assert st == b.HTS_ERR_NONFINITE, b.status_string(st)
+        assert info == [0, which, i + 1, j + 1], info
+        hA, hB = _host(dA, dB)
+        assert np.array_equal(hA, A2, equal_nan=True) and np.array_equal(hB, B2, equal_nan=True)
+    # an entry below the band is not read: no error, and the result is the clean pencil's
+    A2 = A.copy()
+    A2[n - 1, 0] = np.nan
+    dA, dB = _dev(A2, B)
+    dQ, dZ = _empty(n), _empty(n)
+    red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=4)
+    st, info = red.sync_status()
+    assert st == b.HTS_OK, (b.status_string(st), info)
+    H, T, Q, Z = _host(dA, dB, dQ, dZ)
+    _check_invariants(A, B, H, T, Q, Z, 1e-14 * n)
+
+
+def test_nonfinite_update_factor_and_full_reduction(red):
+    n, r = 48, 4
+    A, B = random_rht_pencil(n, r, 6)
+    Q0 = np.eye(n)
+    Q0[7, 9] = np.nan
+    dA, dB = _dev(A, B)
+    dQ, = _dev(Q0)
+    dZ = _empty(n)
+    red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_UPDATE, compz=b.HTS_COMP_INIT, q=2)
+    st, info = red.sync_status()
+    assert st == b.HTS_ERR_NONFINITE and info == [0, 2, 8, 10], (st, info)
+    # the full reduction reads all of A and B: an entry far below the band is reported
+    Ad, Bd = random_pencil(n, 7)
+    Ad[n - 1, 0] = np.nan
+    dA, dB = _dev(Ad, Bd)
+    red.reduce(dA, dB, r, _empty(n), _empty(n), compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT)
+    st, info = red.sync_status()
+    assert st == b.HTS_ERR_NONFINITE and info == [0, 0, n, 1], (st, info)
+    # stage 1 ignores the strictly lower part of B
+    Bt = np.triu(Bd)
+    Bt[n - 1, 0] = np.nan
+    Ad[n - 1, 0] = 1.0
+    dA, dB = _dev(Ad, Bt)
+    dQ, dZ = _empty(n), _empty(n)
+    red.stage1(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT)
+    st, info = red.sync_status()
+    assert st == b.HTS_OK, (b.status_string(st), info)
+    # the context serves the next call
+    A, B = random_rht_pencil(n, r, 8)
+    dA, dB = _dev(A, B)
+    dQ, dZ = _empty(n), _empty(n)
+    red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=2)
+    st, info = red.sync_status()
+    assert st == b.HTS_OK, (b.status_string(st), info)
+    H, T, Q, Z = _host(dA, dB, dQ, dZ)
+    _check_invariants(A, B, H, T, Q, Z, 1e-14 * n)
+
+
+def test_nonfinite_batched_skips_only_that_pencil(red):
+    sizes = [40, 64, 33, 100, 57]
+    rs = [min(8, s // 8) for s in sizes]
+    pencils = [random_pencil(s, 40 + i) for i, s in enumerate(sizes)]
+    bad = 2
+    Ab, Bb = pencils[bad]
+    Bb = Bb.copy()
+    Bb[5, 6] = np.nan
+    pencils[bad] = (Ab, Bb)
+    dA = [_dev(P[0])[0] for P in pencils]
+    dB = [_dev(P[1])[0] for P in pencils]
+    dQ = [_empty(s) for s in sizes]
+    dZ = [_empty(s) for s in sizes]
+    work = torch.empty(max(256, b.hts_workspace_size_batched(sizes, rs)), dtype=torch.uint8, device="cuda")
+    st = b.hts_reduce_batched(red.ctx, sizes, rs, dA, sizes, dB, sizes, b.HTS_COMP_INIT, dQ, sizes,
+                              b.HTS_COMP_INIT, dZ, sizes, b.HTS_GEMM_FP64, None, work, work.numel())
+    assert st == b.HTS_OK
+    st, info = red.sync_status()
+    assert st == b.HTS_ERR_NONFINITE and info == [bad, 1, 6, 7], (st, info)
+    for i, s in enumerate(sizes):
+        if i == bad:
+            continue
+        H, T, Q, Z = _host(dA[i], dB[i], dQ[i], dZ[i])
+        _check_invariants(pencils[i][0], pencils[i][1], H, T, Q, Z, 1e-14 * s)
+
+
+# ---------------------------------------------------------------------------------------
+# ill-conditioned B (the family of the n = 12000, r = 32 configuration) against the oracle
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,r,q,direct", [(384, 8, 8, False), (384, 16, 16, False), (384, 16, 16, True),
+                                          (300, 16, 7, False), (320, 32, 32, False)])
+def test_ill_conditioned_stage2_matches_oracle(red, oracle_mod, n, r, q, direct):
+    A, B = ill_conditioned_rht_pencil(n, r, 31 + r + q)
+    dA, dB = _dev(A, B)
+    dQ, dZ = _empty(n), _empty(n)
+    b.hts_fallback_count(red.ctx)   # reset the counter
+    red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q,
+               flags=b.HTS_FLAG_TEST_DIRECT_RQ if direct else 0)
+    st, info = red.sync_status()
+    assert st == b.HTS_OK, (b.status_string(st), info)
+    fallbacks = b.hts_fallback_count(red.ctx)
+    H, T, Q, Z = _host(dA, dB, dQ, dZ)
+    c = _check_invariants(A, B, H, T, Q, Z, 1e-14 * n)
+    Ho, To, Qo, Zo = oracle_mod.stage2(A, B, r)
+    g, o = canonical(H, T, Q, Z), canonical(Ho, To, Qo, Zo)
+    scale = max(1.0, float(np.abs(A).max()), float(np.abs(B).max()))
+    err = max(float(np.abs(x - y).max()) for x, y in zip(g, o)) / scale
+    print("ill-conditioned stage 2 n=%d r=%d q=%d direct_rq=%s: max |GPU - oracle| = %.2e, "
+          "RQ fallbacks %d, %s" % (n, r, q, direct, err, fallbacks, c))
+    assert err <= 1e-12 * n, err
+    if direct or r > 16:
+        assert fallbacks == 0
+
+
+@pytest.mark.parametrize("n,r", [(256, 8), (384, 16), (384, 32)])
+def test_ill_conditioned_reduce_matches_oracle(red, oracle_mod, n, r):
+    A, B = ill_conditioned_pencil(n, 3)
+    dA, dB = _dev(A, B)
+    dQ, dZ = _empty(n), _empty(n)
+    red.reduce(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT)
+    st, info = red.sync_status()
+    assert st == b.HTS_OK, (b.status_string(st), info)
+    H, T, Q, Z = _host(dA, dB, dQ, dZ)
+    c = _check_invariants(A, B, H, T, Q, Z, 1e-14 * n)
+    Ho, To, Qo, Zo = oracle_mod.reduce(A, B, r)
+    g = canonical(H, T, Q, Z, B_in=B)
+    o = canonical(Ho, To, Qo, Zo, B_in=B)
+    scale = max(float(np.abs(A).max()), float(np.abs(B).max()))
+    err = max(float(np.abs(x - y).max()) for x, y in zip(g, o)) / scale
+    print("ill-conditioned reduce n=%d r=%d: max |GPU - oracle| = %.2e, %s" % (n, r, err, c))
+    assert err <= 1e-12 * n, err
+
+
+# ---------------------------------------------------------------------------------------
+# saddle-point pencils (a quarter of the eigenvalues infinite)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,r,mode", [(256, 8, b.HTS_GEMM_FP64), (400, 16, b.HTS_GEMM_FP64),
+                                      (400, 16, b.HTS_GEMM_EMU_BF16)])
+def test_saddle_point_reduce_invariants(red, n, r, mode):
+    A, B = saddle_point_pencil(n, 11 + n)
+    dA, dB = _dev(A, B)
+    dQ, dZ = _empty(n), _empty(n)
+    red.reduce(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, mode=mode)
+    st, info = red.sync_status()
+    assert st == b.HTS_OK, (b.status_string(st), info)
+    H, T, Q, Z = _host(dA, dB, dQ, dZ)
+    _check_invariants(A, B, H, T, Q, Z, 1e-14 * n)
+    assert np.array_equal(Z[:, 0], np.eye(n)[:, 0])
+    # T = Q^T B Z has rank m = n - n // 8 and is triangular, so at least n // 8 of its
+    # diagonal entries vanish (up to rounding)
+    d = np.sort(np.abs(np.diag(T)))
+    assert d[n // 8 - 1] < 1e-12 * n, d[: n // 8 + 2]

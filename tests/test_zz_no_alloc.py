@@ -54,9 +54,12 @@ def test_noalloc_matches_workspace_entry_point():
             assert float(np.abs(x - y).max()) <= tol
         assert np.abs(np.tril(got[0], -2)).max() == 0.0 and np.abs(np.tril(got[1], -1)).max() == 0.0
 
-    # a pencil whose workspace exceeds the fixed array is rejected before anything runs
-    big = 1 << 20
-    st = b.hts_reduce_stage2_noalloc(red.ctx, 40000, 32, big, 40000, big, 40000, b.HTS_COMP_NONE, None, 1,
-                                     b.HTS_COMP_NONE, None, 1, b.HTS_GEMM_FP64, None)
-    assert st == b.HTS_ERR_WORKSPACE
+    # a pencil whose scratch exceeds the fixed array is rejected before anything runs; the size
+    # check comes first, and the matrices are NULL, so that a regression of that check ends in
+    # an argument error on the host rather than in a launch
+    for mode in (b.HTS_GEMM_FP64, b.HTS_GEMM_EMU_BF16):
+        st = b.hts_reduce_stage2_noalloc(red.ctx, 40000, 32 if mode == b.HTS_GEMM_FP64 else 16, None, 40000,
+                                         None, 40000, b.HTS_COMP_NONE, None, 1, b.HTS_COMP_NONE, None, 1, mode,
+                                         None)
+        assert st == b.HTS_ERR_WORKSPACE, b.status_string(st)
     red.close()
