@@ -72,6 +72,9 @@ typedef enum {
  *             only value this build implements; others give HTS_ERR_UNSUPPORTED).
  *  tile_m, tile_n  reserved.
  *  flags      bit 0 (HTS_FLAG_NO_CLEAN): skip the final exact zeroing below the band.
+ *             bit 1 (HTS_FLAG_SERIAL_UPDATES): run each group's delayed updates after its
+ *             chase instead of beside the next group's chase (the look-ahead of Section
+ *             "Parallel stage two", the default); same results up to rounding, for comparison.
  *             bit 30 (HTS_FLAG_TEST_STALL): fault injection for tests of the failure path:
  *             the chase block of the first sweep never publishes its progress, so the next
  *             block's bounded wait (2 s) runs out and HTS_ERR_TIMEOUT is reported by
@@ -90,6 +93,7 @@ typedef struct {
 } hts_params;
 
 #define HTS_FLAG_NO_CLEAN 1
+#define HTS_FLAG_SERIAL_UPDATES 2
 #define HTS_FLAG_TEST_STALL (1 << 30)
 #define HTS_FLAG_TEST_DIRECT_RQ (1 << 29)
 

@@ -26,6 +26,8 @@ enum {
     HTS_K_EMU_RIGHT = 8,    /* emulated-FP64 delayed right updates of A and B (stage 2) */
     HTS_K_EMU_LEFT = 9,     /* emulated-FP64 delayed left updates of A and B (stage 2) */
     HTS_K_EMU_QZ = 10,      /* emulated-FP64 delayed updates of Q and Z (stage 2, side stream) */
+    HTS_K_UPDATE = 11,      /* look-ahead update launch: a group's A / B updates and the previous
+                               group's Q / Z update, beside the next group's chase (stage 2) */
     HTS_K_NKINDS = 12
 };
 

@@ -30,6 +30,7 @@ HTS_GEMM_FP64 = 0
 HTS_GEMM_EMU_BF16 = 1
 
 HTS_FLAG_NO_CLEAN = 1
+HTS_FLAG_SERIAL_UPDATES = 2
 HTS_FLAG_TEST_STALL = 1 << 30
 HTS_FLAG_TEST_DIRECT_RQ = 1 << 29
 
@@ -42,7 +43,7 @@ class hts_params(ctypes.Structure):
 HTS_K_NKINDS = 12
 KERNEL_KINDS = {0: "k_s2_generate", 1: "k_s2_apply_right", 2: "k_s2_apply_left", 3: "util", 4: "stage1",
                 5: "k_s2_apply_right_qz", 6: "k_reduce_batched", 7: "k_s2_form_u", 8: "k_s2_emu_apply_right",
-                9: "k_s2_emu_apply_left", 10: "k_s2_emu_apply_qz"}
+                9: "k_s2_emu_apply_left", 10: "k_s2_emu_apply_qz", 11: "k_s2_update"}
 
 
 class hts_kernel_profile(ctypes.Structure):

@@ -27,7 +27,7 @@
 //   8. publish block k of sweep j.
 // Block-level updates use groups of 8 lanes per row or column (3-level reductions), so one
 // round covers up to 32 rows.
-#include "hts_internal.cuh"
+#include "schedule.cuh"
 
 namespace hts {
 
@@ -116,11 +116,18 @@ __global__ void __launch_bounds__(kGenThreads) k_s2_generate(GenArgs a)
         return;
     }
 
+    __shared__ UpdWait uw;   // the previous group's update tiles (look-ahead), checked by thread 0
+    if (tid == 0) uw.init(a.uflags, a.uplan, a.uepoch, n);
     for (int k = 0; k < kl; ++k) {
         // ---- wait until sweep j-1 has finished block k+2 (or all of its blocks), and its helper
         //      block k+1: the helper's rows of block k+1 include the upper rows of this step's
-        //      newest B column (read by the prefetch) and share column i2 with this step's band
-        if (tid == 0 && s > 0)
+        //      newest B column (read by the prefetch) and share column i2 with this step's band;
+        //      and until the previous group's update has finished the tiles this step touches
+        if (tid == 0) {
+            const StepGeom gk = step_geom(n, r, j1, qg, k, j);
+            s_abort = !uw.wait_for(gk.i2, gk.i3, a.status, a.group, k, j);
+        }
+        if (tid == 0 && s > 0 && !s_abort)
             s_abort = !(wait_at_least(a.flags + s - 1, a.epoch | (unsigned long long)imin(k + 3, kl_prev), a.status,
                                       a.group, k, j) &&
                         wait_at_least(hflags + s - 1, a.epoch | (unsigned long long)(k + 2), a.status, a.group, k, j));

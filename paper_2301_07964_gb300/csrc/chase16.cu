@@ -37,7 +37,7 @@
 //   6. publish block k of sweep j.
 // Reflectors are stored as (u, tau) with H = I - tau u u^T, u = x - beta e_1, tau = 2/|u|^2 and
 // beta = -sign(x_1) |x| (the sign of LAPACK's dlarfg); tau = 0 is the identity.
-#include "hts_internal.cuh"
+#include "schedule.cuh"
 
 namespace hts {
 
@@ -414,8 +414,17 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
                wait_at_least(hflags + s - 1, a.epoch | (unsigned long long)(k + 2), a.status, a.group, k, j);
     };
 
+    // the previous group's update tiles this sweep's steps touch (look-ahead): thread 128
+    // checks them step by step before the step's loads
+    __shared__ UpdWait uw;   // thread 128's progress through those tiles
+    if (tid == 128) uw.init(a.uflags, a.uplan, a.uepoch, n);
+    auto wait_upd = [&](int k) -> bool {
+        const StepGeom gk = step_geom(n, r, j1, qg, k, j);
+        return uw.wait_for(gk.i2, gk.i3, a.status, a.group, k, j);
+    };
+
     // step 0's dependencies and data
-    if (tid == 128 && s > 0) s_abort = !wait_deps(0);
+    if (tid == 128) s_abort = !(wait_upd(0) && (s == 0 || wait_deps(0)));
     __syncthreads();
     if (s_abort) return;
     StepInfo I = step_info(n, r, j1, qg, kg, 0, j);
@@ -723,7 +732,7 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
             __syncthreads();
 
             // warp 4 takes the next step's dependencies while Z^ and the band update run
-            if (attempt == 0 && tid == 128 && s > 0 && k + 1 < kl) s_abort = !wait_deps(k + 1);
+            if (attempt == 0 && tid == 128 && k + 1 < kl) s_abort = !(wait_upd(k + 1) && (s == 0 || wait_deps(k + 1)));
 
             if (gen) {
                 // ---- 5. opposite reflector Z^ from z (panel); band dots (warps 5 .. 7)

@@ -25,6 +25,7 @@
 // of the window's largest entry.  No FP64 instruction runs in the update loop: FP64 values enter and leave
 // through integer bit manipulation of their IEEE-754 encoding.
 #include "right_window.cuh"
+#include "schedule.cuh"
 
 namespace hts {
 
@@ -141,10 +142,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-__device__ __forceinline__ void named_barrier(int id, int nthreads)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
 
 }  // namespace
 
@@ -232,15 +229,15 @@ struct EmuSmem {
 
 template <int HALF>
 __device__ __forceinline__ void emu_worker(const EmuArgs &a, EmuSmem &S, int kind, double *X, size_t ld,
-                                           const uint2 *P, int l0, int kbeg, int kend)
+                                           const uint2 *P, int l0, int kbeg, int kend, int tid, int wb)
 {
-    const int tid = threadIdx.x, lane = tid & 31, slab = (tid >> 5) >> 1;
+    const int lane = tid & 31, slab = (tid >> 5) >> 1;
     const int g = lane >> 2, c = lane & 3;
     const int n = a.n, r = a.r, j1 = a.j1, qg = a.qg;
     const int w = r + qg - 1;
     const int jl = j1 + qg - 1;
     const bool left = kind >= 4;
-    const int bar = 1 + slab;
+    const int bar = wb + 1 + slab;
     const int lineA = l0 + slab * 16 + g, lineB = lineA + 8;   // lines of rr = 0, 1
     auto addr = [=](int ln, int p, int k) -> double * {
         const int pos = j1 + k * r + 1 + p;   // matrix column (right) or row (left)
@@ -315,7 +312,7 @@ __device__ __forceinline__ void emu_worker(const EmuArgs &a, EmuSmem &S, int kin
                         S.carry[slab][(rr * 2 + h) * 2 + pr][lane] = refix(xc[rr][h][pr], uc[rr], ua[rr]);
             }
         }
-        named_barrier(bar, 64);
+        group_sync(bar, 64);
         if (HALF == 1) {
 #pragma unroll
             for (int rr = 0; rr < 2; ++rr) {
@@ -361,7 +358,7 @@ __device__ __forceinline__ void emu_worker(const EmuArgs &a, EmuSmem &S, int kin
 #pragma unroll
         for (int t = 0; t < kDigits; ++t)
             S.dig[slab][HALF][t][lane] = make_uint4(af[t][HALF][0], af[t][HALF][1], af[t][HALF][2], af[t][HALF][3]);
-        named_barrier(bar, 64);
+        group_sync(bar, 64);
 #pragma unroll
         for (int t = 0; t < kDigits; ++t) {
             const uint4 o = S.dig[slab][HALF ^ 1][t][lane];
@@ -380,7 +377,7 @@ __device__ __forceinline__ void emu_worker(const EmuArgs &a, EmuSmem &S, int kin
         }
 
         cp_async_wait<1>();
-        __syncthreads();
+        group_sync(wb, kEmuThreads);
         const uint2 *pl = S.planes[buf];
 
         // ---- products for this half's two n-tiles; results replace xv
@@ -420,7 +417,7 @@ __device__ __forceinline__ void emu_worker(const EmuArgs &a, EmuSmem &S, int kin
                 xv[rr][h][pr] = act ? val : refix(xv[rr][h][pr], ua[rr], ua[rr] + 3);
             }
         }
-        __syncthreads();   // planes[buf] is refilled by the next iteration's copy
+        group_sync(wb, kEmuThreads);   // planes[buf] is refilled by the next iteration's copy
 
         // ---- positions leaving the window; half 0 keeps the carry
 #pragma unroll
@@ -440,13 +437,13 @@ __device__ __forceinline__ void emu_worker(const EmuArgs &a, EmuSmem &S, int kin
     }
 }
 
-__global__ void __launch_bounds__(kEmuThreads) k_s2_emu_apply(EmuArgs a)
+// One tile of an emulated delayed update: lines tile*32+1 .. of matrix a.M[mi], by the 128
+// threads tid = 0..127 of a group whose barrier is wb (slab barriers wb+1, wb+2).  Right
+// updates of A and B also run the tile's staircase blocks in native FP64.
+__device__ __forceinline__ void emu_tile(const EmuArgs &a, EmuSmem &S, int mi, int tile, int tid, int wb)
 {
-    extern __shared__ __align__(16) unsigned char emu_smem[];
-    EmuSmem &S = *reinterpret_cast<EmuSmem *>(emu_smem);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int warp = tid >> 5;
     const int n = a.n, r = a.r, j1 = a.j1, qg = a.qg;
-    const int mi = blockIdx.y;
     const int kind = a.kind[mi];
     const bool left = kind >= 4;
     double *X = a.M[mi];
@@ -454,10 +451,7 @@ __global__ void __launch_bounds__(kEmuThreads) k_s2_emu_apply(EmuArgs a)
     const uint2 *P = (kind == 3 || left) ? a.planesQ : a.planesZ;
     const int kmax = nblocks_gen(n, r, j1) - 1;
     const int jl = j1 + qg - 1;
-    if (__ldcg(a.status) != 0) return;
 
-    // lines of this block; left updates walk the column tiles from the right
-    const int tile = left ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
     const int l0 = tile * kEmuRows + 1;
     const int llast = imin(l0 + kEmuRows - 1, n);
     int kbeg = kmax, kend = 0;
@@ -489,15 +483,48 @@ __global__ void __launch_bounds__(kEmuThreads) k_s2_emu_apply(EmuArgs a)
             for (int e = tid; e < kPlaneWords / 2; e += kEmuThreads) cp_async16(dst + e, src + e);
             cp_async_commit();
         }
-        if (warp & 1) emu_worker<1>(a, S, kind, X, ld, P, l0, kbeg, kend);
-        else emu_worker<0>(a, S, kind, X, ld, P, l0, kbeg, kend);
+        if (warp & 1) emu_worker<1>(a, S, kind, X, ld, P, l0, kbeg, kend, tid, wb);
+        else emu_worker<0>(a, S, kind, X, ld, P, l0, kbeg, kend, tid, wb);
         cp_async_wait<0>();
     }
     if (kind <= 1 && skstop <= skstart) {
-        __syncthreads();   // the tile's emulated results are stored; shared memory is reused
+        group_sync(wb, kEmuThreads);   // the tile's emulated results are stored; shared memory is reused
         right_window_rows<kEmuThreads>(X, (int)ld, kind, a.R.VZ, a.R.TZ, a.R.kdim, n, r, j1, qg, l0, skstart,
-                                       skstop, reinterpret_cast<double *>(emu_smem));
+                                       skstop, reinterpret_cast<double *>(&S), tid, wb);
     }
+}
+
+__global__ void __launch_bounds__(kEmuThreads) k_s2_emu_apply(EmuArgs a)
+{
+    extern __shared__ __align__(16) unsigned char emu_smem[];
+    EmuSmem &S = *reinterpret_cast<EmuSmem *>(emu_smem);
+    if (__ldcg(a.status) != 0) return;
+    const int kind = a.kind[blockIdx.y];
+    // left updates walk the column tiles from the right
+    const int tile = kind >= 4 ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    emu_tile(a, S, blockIdx.y, tile, threadIdx.x, 0);
+}
+
+// ---------------------------------------------------------------------------------------
+// Look-ahead update launch (schedule.cuh): one block per SM with kUpdEmuWorkers independent
+// workers of 128 threads, each with its own shared memory and barriers (ids 3w+1 .. 3w+3), taking
+// the tiles of the group's A / B updates and of the previous group's Q / Z update in ticket order.
+// The blocks leave the remaining SMs to the chase of the next group, which runs beside them.
+// ---------------------------------------------------------------------------------------
+constexpr int kUpdEmuWorkers = 3;
+
+__global__ void __launch_bounds__(kEmuThreads * kUpdEmuWorkers, 1) k_s2_update_emu(UpdEmuArgs a)
+{
+    extern __shared__ __align__(16) unsigned char upd_smem[];
+    __shared__ int slot[kUpdEmuWorkers];
+    const int worker = threadIdx.x / kEmuThreads, tid = threadIdx.x % kEmuThreads;
+    EmuSmem &S = reinterpret_cast<EmuSmem *>(upd_smem)[worker];
+    const int wb = 1 + 3 * worker;
+    update_worker<kEmuThreads>(a.s, tid, wb, &slot[worker], [&](const Task &T) {
+        if (T.kind == kTaskRight) emu_tile(a.right, S, T.mat, T.tile, tid, wb);
+        else if (T.kind == kTaskLeft) emu_tile(a.left, S, T.mat, T.tile, tid, wb);
+        else if (T.kind == kTaskQZ) emu_tile(a.qz, S, T.mat, T.tile, tid, wb);
+    });
 }
 
 // ---------------------------------------------------------------------------------------
@@ -513,6 +540,17 @@ cudaError_t launch_s2_form_u(const FormUArgs &a, cudaStream_t st)
     if (kmax < 0) return cudaSuccess;
     dim3 grid((kmax + 1 + 3) / 4, 2);
     k_s2_form_u<<<grid, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+int update_emu_workers() { return kUpdEmuWorkers; }
+
+cudaError_t launch_s2_update_emu(const UpdEmuArgs &a, int ctas, cudaStream_t st)
+{
+    const int sm = (int)(kUpdEmuWorkers * sizeof(EmuSmem));
+    cudaError_t e = cudaFuncSetAttribute(k_s2_update_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    k_s2_update_emu<<<ctas, kEmuThreads * kUpdEmuWorkers, sm, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,7 @@
 #include <cstring>
 #include <vector>
 
-#include "hts_internal.cuh"
+#include "schedule.cuh"
 
 namespace hts {
 
@@ -26,14 +26,19 @@ struct DeviceGuard {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Workspace layout of stage 2: two reflector sets (group g uses set g mod 2, so the Q / Z
-// update of group g can still read its set while group g+1 generates into the other one), one
-// progress word per sweep slot and, for the emulated updates, the digit planes of the
-// blocks' reflector products (one plane set per reflector set).
+// Workspace layout of stage 2: three reflector sets (group g uses set g mod 3; the look-ahead
+// update of group g+1 still reads set g for its Q / Z part while group g+2 generates into the
+// next one), one progress word per sweep slot and helper, the tile flags and ticket counters of
+// the look-ahead updates and, for the emulated updates, the digit planes of the blocks'
+// reflector products (one plane set per reflector set).  The words from off_flags up to
+// total_fp64 are cleared at the start of every call.
+constexpr int kSets = 3;
+
 struct S2Layout {
-    int kdim, qmax;
-    size_t off_vq[2], off_tq[2], off_vz[2], off_tz[2], off_gram[2], off_flags, total_fp64;
-    size_t off_pq[2], off_pz[2], total;
+    int kdim, qmax, ntiles, nticket;
+    size_t off_vq[kSets], off_tq[kSets], off_vz[kSets], off_tz[kSets], off_gram[kSets];
+    size_t off_flags, off_tflags, off_tick, total_fp64;
+    size_t off_pq[kSets], off_pz[kSets], total;
 };
 
 S2Layout s2_layout(int n, int r)
@@ -44,7 +49,7 @@ S2Layout s2_layout(int n, int r)
     const size_t nv = (size_t)L.qmax * L.kdim * r * sizeof(double);
     const size_t nt = (size_t)L.qmax * L.kdim * sizeof(double);
     size_t o = 0;
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kSets; ++b) {
         L.off_vq[b] = o; o = align_up(o + nv, 256);
         L.off_tq[b] = o; o = align_up(o + nt, 256);
         L.off_vz[b] = o; o = align_up(o + nv, 256);
@@ -53,9 +58,13 @@ S2Layout s2_layout(int n, int r)
         if (r <= 16) o = align_up(o + (size_t)L.kdim * L.qmax * L.qmax * sizeof(double), 256);
     }
     L.off_flags = o; o = align_up(o + 2 * (size_t)L.qmax * sizeof(unsigned long long), 256);
+    L.ntiles = (n + kTileLines - 1) / kTileLines;
+    L.off_tflags = o; o = align_up(o + 4 * (size_t)L.ntiles * sizeof(unsigned long long), 256);
+    L.nticket = n + 2;   // one per update launch: at most n - 2 groups plus the closing Q / Z launch
+    L.off_tick = o; o = align_up(o + (size_t)L.nticket * sizeof(unsigned), 256);
     L.total_fp64 = o;
     const size_t np = emu_plane_bytes(L.kdim);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kSets; ++b) {
         L.off_pq[b] = o; o = align_up(o + np, 256);
         L.off_pz[b] = o; o = align_up(o + np, 256);
     }
@@ -224,146 +233,244 @@ size_t stage2_workspace_bytes(int n, int r) { return s2_layout(n, r).total_fp64;
 // ... and in the given update mode (the emulated mode adds the digit planes).
 size_t stage2_workspace_bytes_mode(int n, int r, hts_gemm_mode mode) { return s2_bytes(n, r, mode); }
 
-// Stage 2 driver: the group loop of generate / apply launches.
+namespace {
+
+struct S2Ptrs {
+    ReflectorSet R[kSets];
+    uint2 *PQ[kSets], *PZ[kSets];
+    double *gram[kSets];
+    unsigned long long *fl, *tfl;
+    unsigned *tick;
+};
+
+S2Ptrs s2_ptrs(const S2Layout &L, void *work)
+{
+    S2Ptrs P;
+    char *w = static_cast<char *>(work);
+    for (int b = 0; b < kSets; ++b) {
+        P.PQ[b] = reinterpret_cast<uint2 *>(w + L.off_pq[b]);
+        P.PZ[b] = reinterpret_cast<uint2 *>(w + L.off_pz[b]);
+        P.R[b].VQ = reinterpret_cast<double *>(w + L.off_vq[b]);
+        P.R[b].TQ = reinterpret_cast<double *>(w + L.off_tq[b]);
+        P.R[b].VZ = reinterpret_cast<double *>(w + L.off_vz[b]);
+        P.R[b].TZ = reinterpret_cast<double *>(w + L.off_tz[b]);
+        P.R[b].kdim = L.kdim;
+        P.gram[b] = reinterpret_cast<double *>(w + L.off_gram[b]);
+    }
+    P.fl = reinterpret_cast<unsigned long long *>(w + L.off_flags);
+    P.tfl = reinterpret_cast<unsigned long long *>(w + L.off_tflags);
+    P.tick = reinterpret_cast<unsigned *>(w + L.off_tick);
+    return P;
+}
+
+EmuArgs emu_args(double *M0, int ld0, int kind0, double *M1, int ld1, int kind1, int n, int r, int j1, int qg,
+                 const S2Ptrs &P, int set, const int *status)
+{
+    EmuArgs e;
+    e.M[0] = M0; e.ld[0] = ld0; e.kind[0] = kind0;
+    e.M[1] = M1; e.ld[1] = ld1; e.kind[1] = kind1;
+    for (int i = 2; i < 4; ++i) { e.M[i] = nullptr; e.ld[i] = 1; e.kind[i] = 0; }
+    e.n = n; e.r = r; e.j1 = j1; e.qg = qg;
+    e.planesQ = P.PQ[set]; e.planesZ = P.PZ[set]; e.R = P.R[set]; e.status = status;
+    return e;
+}
+
+ApplyArgs apply_args(double *M0, int ld0, int kind0, double *M1, int ld1, int kind1, int n, int r, int j1, int qg,
+                     const S2Ptrs &P, int set, const int *status)
+{
+    ApplyArgs a;
+    a.M[0] = M0; a.ld[0] = ld0; a.kind[0] = kind0;
+    a.M[1] = M1; a.ld[1] = ld1; a.kind[1] = kind1;
+    for (int i = 2; i < 4; ++i) { a.M[i] = nullptr; a.ld[i] = 1; a.kind[i] = 0; }
+    a.n = n; a.r = r; a.j1 = j1; a.qg = qg; a.R = P.R[set]; a.status = status;
+    return a;
+}
+
+// One look-ahead update launch (schedule.cuh): A / B updates of the group (j1, qg, set), Q / Z
+// update of the group (pj1, pqg, pset), persistent blocks on the SMs the next chase leaves free.
+cudaError_t launch_update(hts_ctx *ctx, bool emu, const UpdSched &us, double *A, int lda, double *B, int ldb,
+                          double *const *qzM, const int *qzld, const int *qzkind, int n, int r, int j1, int qg,
+                          int set, int pj1, int pqg, int pset, int q, const S2Ptrs &P, cudaStream_t st)
+{
+    if (us.P.total <= 0) return cudaSuccess;
+    const int workers = emu ? update_emu_workers() : update_fp64_workers();
+    int ctas = imax(1, ctx->num_sms - 2 * q);
+    ctas = imin(ctas, (us.P.total + workers - 1) / workers);
+    int *status = ctx->d_status;
+    if (emu) {
+        UpdEmuArgs ua;
+        ua.right = emu_args(A, lda, 0, B, ldb, 1, n, r, j1, qg, P, set, status);
+        ua.left = emu_args(A, lda, 4, B, ldb, 5, n, r, j1, qg, P, set, status);
+        ua.qz = emu_args(qzM[0], qzld[0], qzkind[0], qzM[1], qzld[1], qzkind[1], n, r, pj1, pqg, P, pset, status);
+        ua.s = us;
+        return launch_s2_update_emu(ua, ctas, st);
+    }
+    UpdFp64Args uf;
+    uf.right = apply_args(A, lda, 0, B, ldb, 1, n, r, j1, qg, P, set, status);
+    uf.qz = apply_args(qzM[0], qzld[0], qzkind[0], qzM[1], qzld[1], qzkind[1], n, r, pj1, pqg, P, pset, status);
+    uf.left.A = A; uf.left.B = B; uf.left.lda = lda; uf.left.ldb = ldb;
+    uf.left.n = n; uf.left.r = r; uf.left.j1 = j1; uf.left.qg = qg; uf.left.R = P.R[set]; uf.left.status = status;
+    uf.s = us;
+    uf.smem_doubles = update_fp64_smem_doubles(r, q);
+    return launch_s2_update_fp64(uf, ctas, st);
+}
+
+}  // namespace
+
+// Stage 2 driver: the group loop of generate / apply launches.  Default (look-ahead, Section
+// "Parallel stage two"): per group g on the caller's stream the chase (Alg. 3) and, in emulated
+// mode, the block formation; then on the update stream one persistent launch with g's A / B
+// updates and g-1's Q / Z update (Alg. 4), beside the chase of group g+1, which waits tile by
+// tile for the A / B elements it touches (schedule.cuh).  With HTS_FLAG_SERIAL_UPDATES each
+// group's A / B updates follow its chase on the caller's stream and only the Q / Z update
+// overlaps the next chase (side stream).
 hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B, int ldb,
                       double *Q, int ldq, double *Z, int ldz, int q, int flags, hts_gemm_mode mode,
                       void *work, cudaStream_t st)
 {
     if (n <= 2 || r <= 1) return HTS_OK;
     const S2Layout L = s2_layout(n, r);
-    char *w = static_cast<char *>(work);
+    const S2Ptrs P = s2_ptrs(L, work);
     const bool emu = mode == HTS_GEMM_EMU_BF16;
-    ReflectorSet R[2];
-    uint2 *PQ[2], *PZ[2];
-    for (int b = 0; b < 2; ++b) {
-        PQ[b] = reinterpret_cast<uint2 *>(w + L.off_pq[b]);
-        PZ[b] = reinterpret_cast<uint2 *>(w + L.off_pz[b]);
-        R[b].VQ = reinterpret_cast<double *>(w + L.off_vq[b]);
-        R[b].TQ = reinterpret_cast<double *>(w + L.off_tq[b]);
-        R[b].VZ = reinterpret_cast<double *>(w + L.off_vz[b]);
-        R[b].TZ = reinterpret_cast<double *>(w + L.off_tz[b]);
-        R[b].kdim = L.kdim;
-    }
-    unsigned long long *fl = reinterpret_cast<unsigned long long *>(w + L.off_flags);
-    cudaError_t e = cudaMemsetAsync(fl, 0, 2 * (size_t)L.qmax * sizeof(unsigned long long), st);
+    const bool lookahead = !(flags & HTS_FLAG_SERIAL_UPDATES);
+    int *status = ctx->d_status;
+    cudaError_t e = cudaMemsetAsync(static_cast<char *>(work) + L.off_flags, 0, L.total_fp64 - L.off_flags, st);
     if (e != cudaSuccess) return HTS_ERR_CUDA;
     const bool qz = (Q != nullptr) || (Z != nullptr);
-    cudaStream_t side = ctx->side;
+    const int nqz = (Z ? 1 : 0) + (Q ? 1 : 0);
+    double *qzM[2] = {Z ? Z : Q, Z ? Q : nullptr};
+    const int qzld[2] = {Z ? ldz : ldq, ldq};
+    const int qzkind[2] = {Z ? 2 : 3, 3};
+    cudaStream_t side = lookahead ? ctx->upd : ctx->side;
 
-    int group = 0;
+    int group = 0, prev_set = 0, prev_j1 = 0, prev_qg = 0;
+    TaskPlan prev_plan = task_plan(n, r, 1, 1, false, 0);
+    GroupCost prev_gc{};
     for (int j1 = 1; j1 <= n - 2; j1 += q, ++group) {
         const int qg = imin(q, n - 2 - j1 + 1);
-        const int set = group & 1;
+        const int set = group % kSets;
         const GroupCost gc = ctx->prof.enabled ? s2_group_cost(n, r, j1, qg, Q != nullptr, Z != nullptr, emu)
                                                : GroupCost{};
-        // the Q / Z update of group-2 must be done with this reflector set
-        if (qz && group >= 2 && cudaStreamWaitEvent(st, ctx->ev_qz[set], 0) != cudaSuccess) return HTS_ERR_CUDA;
+        // set g mod 3 was last read by the update launch of group g-2 (Q / Z of group g-3)
+        if (lookahead && group >= 2 && cudaStreamWaitEvent(st, ctx->ev_upd[(group - 2) % kSets], 0) != cudaSuccess)
+            return HTS_ERR_CUDA;
+        if (!lookahead && qz && group >= 3 && cudaStreamWaitEvent(st, ctx->ev_qz[set], 0) != cudaSuccess)
+            return HTS_ERR_CUDA;
 
         GenArgs ga;
         ga.A = A; ga.B = B; ga.lda = lda; ga.ldb = ldb;
         ga.n = n; ga.r = r; ga.j1 = j1; ga.qg = qg; ga.group = group;
-        ga.R = R[set]; ga.flags = fl; ga.qmax = L.qmax;
-        ga.gram = reinterpret_cast<double *>(w + L.off_gram[set]);
+        ga.R = P.R[set]; ga.flags = P.fl; ga.qmax = L.qmax;
+        ga.gram = P.gram[set];
         ga.epoch = (unsigned long long)(group + 1) << 32;
-        ga.status = ctx->d_status;
+        ga.status = status;
         ga.stall = (flags & HTS_FLAG_TEST_STALL) ? 1 : 0;
         ga.direct_rq = (flags & HTS_FLAG_TEST_DIRECT_RQ) ? 1 : 0;
+        ga.uflags = (lookahead && group >= 1) ? P.tfl : nullptr;
+        ga.uplan = prev_plan;
+        ga.uepoch = (unsigned long long)group;   // the previous group's update publishes group
         {
             ProfScope ps(ctx, st);
             e = (r <= 16) ? launch_s2_chase16(ga, st) : launch_s2_generate(ga, st);
             if (e != cudaSuccess) return HTS_ERR_CUDA;
             ps.done(HTS_K_GENERATE, gc.f_gen, gc.b_gen);
         }
-
         if (emu) {
-            // block formation, then the delayed updates as emulated products
             FormUArgs fa;
-            fa.n = n; fa.r = r; fa.j1 = j1; fa.qg = qg; fa.R = R[set];
-            fa.planesQ = PQ[set]; fa.planesZ = PZ[set]; fa.status = ctx->d_status;
-            {
-                ProfScope ps(ctx, st);
-                if ((e = launch_s2_form_u(fa, st)) != cudaSuccess) return HTS_ERR_CUDA;
-                ps.done(HTS_K_FORM_U, gc.f_form, 0.0);
-            }
-            EmuArgs ea;
-            ea.M[0] = A; ea.ld[0] = lda; ea.kind[0] = 0;
-            ea.M[1] = B; ea.ld[1] = ldb; ea.kind[1] = 1;
-            for (int i = 2; i < 4; ++i) { ea.M[i] = nullptr; ea.ld[i] = 1; ea.kind[i] = 0; }
-            ea.n = n; ea.r = r; ea.j1 = j1; ea.qg = qg;
-            ea.planesQ = PQ[set]; ea.planesZ = PZ[set]; ea.R = R[set]; ea.status = ctx->d_status;
-            {
-                // emulated blocks and, per tile, the staircase blocks in native FP64
+            fa.n = n; fa.r = r; fa.j1 = j1; fa.qg = qg; fa.R = P.R[set];
+            fa.planesQ = P.PQ[set]; fa.planesZ = P.PZ[set]; fa.status = status;
+            ProfScope ps(ctx, st);
+            if ((e = launch_s2_form_u(fa, st)) != cudaSuccess) return HTS_ERR_CUDA;
+            ps.done(HTS_K_FORM_U, gc.f_form, 0.0);
+        }
+
+        if (lookahead) {
+            if (cudaEventRecord(ctx->ev_gen[set], st) != cudaSuccess) return HTS_ERR_CUDA;
+            if (cudaStreamWaitEvent(side, ctx->ev_gen[set], 0) != cudaSuccess) return HTS_ERR_CUDA;
+            const int nq = group >= 1 ? nqz : 0;
+            UpdSched us;
+            us.P = task_plan(n, r, j1, qg, true, nq);
+            us.tflags = P.tfl; us.epoch = (unsigned long long)(group + 1); us.ticket = P.tick + group;
+            us.status = status; us.group = group; us.n = n; us.r = r;
+            ProfScope ps(ctx, side);
+            if ((e = launch_update(ctx, emu, us, A, lda, B, ldb, qzM, qzld, qzkind, n, r, j1, qg, set, prev_j1, prev_qg,
+                                   prev_set, q, P, side)) != cudaSuccess)
+                return HTS_ERR_CUDA;
+            ps.done(HTS_K_UPDATE, gc.f_right + gc.f_stair + gc.f_left + (nq ? prev_gc.f_qz : 0.0),
+                    gc.b_right + gc.b_stair + gc.b_left + (nq ? prev_gc.b_qz : 0.0),
+                    emu ? gc.m_right + gc.m_left + (nq ? prev_gc.m_qz : 0.0) : 0.0);
+            if (cudaEventRecord(ctx->ev_upd[group % kSets], side) != cudaSuccess) return HTS_ERR_CUDA;
+            prev_plan = us.P;
+        } else {
+            if (emu) {
+                const EmuArgs ea = emu_args(A, lda, 0, B, ldb, 1, n, r, j1, qg, P, set, status);
                 ProfScope ps(ctx, st);
                 if ((e = launch_s2_emu_apply(ea, 2, st)) != cudaSuccess) return HTS_ERR_CUDA;
                 ps.done(HTS_K_EMU_RIGHT, gc.f_right + gc.f_stair, gc.b_right + gc.b_stair, gc.m_right);
-            }
-        } else {
-            ApplyArgs aa;
-            aa.M[0] = A; aa.ld[0] = lda; aa.kind[0] = 0;
-            aa.M[1] = B; aa.ld[1] = ldb; aa.kind[1] = 1;
-            for (int i = 2; i < 4; ++i) { aa.M[i] = nullptr; aa.ld[i] = 1; aa.kind[i] = 0; }
-            aa.n = n; aa.r = r; aa.j1 = j1; aa.qg = qg; aa.R = R[set]; aa.status = ctx->d_status;
-            ProfScope ps(ctx, st);
-            if ((e = launch_s2_apply_right(aa, 2, st)) != cudaSuccess) return HTS_ERR_CUDA;
-            ps.done(HTS_K_APPLY_RIGHT, gc.f_right, gc.b_right);
-        }
-
-        if (emu) {
-            EmuArgs el;
-            el.M[0] = A; el.ld[0] = lda; el.kind[0] = 4;
-            el.M[1] = B; el.ld[1] = ldb; el.kind[1] = 5;
-            for (int i = 2; i < 4; ++i) { el.M[i] = nullptr; el.ld[i] = 1; el.kind[i] = 0; }
-            el.n = n; el.r = r; el.j1 = j1; el.qg = qg;
-            el.planesQ = PQ[set]; el.planesZ = PZ[set]; el.R = R[set]; el.status = ctx->d_status;
-            ProfScope ps(ctx, st);
-            if ((e = launch_s2_emu_apply(el, 2, st)) != cudaSuccess) return HTS_ERR_CUDA;
-            ps.done(HTS_K_EMU_LEFT, gc.f_left, gc.b_left, gc.m_left);
-        } else {
-            LeftArgs la;
-            la.A = A; la.B = B; la.lda = lda; la.ldb = ldb;
-            la.n = n; la.r = r; la.j1 = j1; la.qg = qg; la.R = R[set]; la.status = ctx->d_status;
-            ProfScope ps(ctx, st);
-            if ((e = launch_s2_apply_left(la, st)) != cudaSuccess) return HTS_ERR_CUDA;
-            ps.done(HTS_K_APPLY_LEFT, gc.f_left, gc.b_left);
-        }
-        // Q and Z: on the side stream after this group's A / B updates, so that they overlap
-        // the next group's chase (which occupies only qg SMs) and not the A / B updates
-        if (qz) {
-            if (cudaEventRecord(ctx->ev_gen[set], st) != cudaSuccess) return HTS_ERR_CUDA;
-            if (cudaStreamWaitEvent(side, ctx->ev_gen[set], 0) != cudaSuccess) return HTS_ERR_CUDA;
-            if (emu) {
-                EmuArgs eq;
-                int nq = 0;
-                if (Z) { eq.M[nq] = Z; eq.ld[nq] = ldz; eq.kind[nq] = 2; ++nq; }
-                if (Q) { eq.M[nq] = Q; eq.ld[nq] = ldq; eq.kind[nq] = 3; ++nq; }
-                for (int i = nq; i < 4; ++i) { eq.M[i] = nullptr; eq.ld[i] = 1; eq.kind[i] = 0; }
-                eq.n = n; eq.r = r; eq.j1 = j1; eq.qg = qg;
-                eq.planesQ = PQ[set]; eq.planesZ = PZ[set]; eq.R = R[set]; eq.status = ctx->d_status;
-                ProfScope ps(ctx, side);
-                if ((e = launch_s2_emu_apply(eq, nq, side)) != cudaSuccess) return HTS_ERR_CUDA;
-                ps.done(HTS_K_EMU_QZ, gc.f_qz, gc.b_qz, gc.m_qz);
+                const EmuArgs el = emu_args(A, lda, 4, B, ldb, 5, n, r, j1, qg, P, set, status);
+                ProfScope pl(ctx, st);
+                if ((e = launch_s2_emu_apply(el, 2, st)) != cudaSuccess) return HTS_ERR_CUDA;
+                pl.done(HTS_K_EMU_LEFT, gc.f_left, gc.b_left, gc.m_left);
             } else {
-                ApplyArgs aq;
-                int nq = 0;
-                if (Z) { aq.M[nq] = Z; aq.ld[nq] = ldz; aq.kind[nq] = 2; ++nq; }
-                if (Q) { aq.M[nq] = Q; aq.ld[nq] = ldq; aq.kind[nq] = 3; ++nq; }
-                for (int i = nq; i < 4; ++i) { aq.M[i] = nullptr; aq.ld[i] = 1; aq.kind[i] = 0; }
-                aq.n = n; aq.r = r; aq.j1 = j1; aq.qg = qg; aq.R = R[set]; aq.status = ctx->d_status;
-                ProfScope ps(ctx, side);
-                if ((e = launch_s2_apply_right(aq, nq, side)) != cudaSuccess) return HTS_ERR_CUDA;
-                ps.done(HTS_K_APPLY_QZ, gc.f_qz, gc.b_qz);
+                const ApplyArgs aa = apply_args(A, lda, 0, B, ldb, 1, n, r, j1, qg, P, set, status);
+                ProfScope ps(ctx, st);
+                if ((e = launch_s2_apply_right(aa, 2, st)) != cudaSuccess) return HTS_ERR_CUDA;
+                ps.done(HTS_K_APPLY_RIGHT, gc.f_right, gc.b_right);
+                LeftArgs la;
+                la.A = A; la.B = B; la.lda = lda; la.ldb = ldb;
+                la.n = n; la.r = r; la.j1 = j1; la.qg = qg; la.R = P.R[set]; la.status = status;
+                ProfScope pl(ctx, st);
+                if ((e = launch_s2_apply_left(la, st)) != cudaSuccess) return HTS_ERR_CUDA;
+                pl.done(HTS_K_APPLY_LEFT, gc.f_left, gc.b_left);
             }
-            if (cudaEventRecord(ctx->ev_qz[set], side) != cudaSuccess) return HTS_ERR_CUDA;
+            // Q and Z on the side stream after this group's A / B updates, beside the next chase
+            if (qz) {
+                if (cudaEventRecord(ctx->ev_gen[set], st) != cudaSuccess) return HTS_ERR_CUDA;
+                if (cudaStreamWaitEvent(side, ctx->ev_gen[set], 0) != cudaSuccess) return HTS_ERR_CUDA;
+                ProfScope ps(ctx, side);
+                if (emu) {
+                    const EmuArgs eq = emu_args(qzM[0], qzld[0], qzkind[0], qzM[1], qzld[1], qzkind[1], n, r, j1, qg, P,
+                                                set, status);
+                    if ((e = launch_s2_emu_apply(eq, nqz, side)) != cudaSuccess) return HTS_ERR_CUDA;
+                    ps.done(HTS_K_EMU_QZ, gc.f_qz, gc.b_qz, gc.m_qz);
+                } else {
+                    const ApplyArgs aq = apply_args(qzM[0], qzld[0], qzkind[0], qzM[1], qzld[1], qzkind[1], n, r, j1,
+                                                    qg, P, set, status);
+                    if ((e = launch_s2_apply_right(aq, nqz, side)) != cudaSuccess) return HTS_ERR_CUDA;
+                    ps.done(HTS_K_APPLY_QZ, gc.f_qz, gc.b_qz);
+                }
+                if (cudaEventRecord(ctx->ev_qz[set], side) != cudaSuccess) return HTS_ERR_CUDA;
+            }
         }
-
+        prev_gc = gc;
+        prev_set = set;
+        prev_j1 = j1;
+        prev_qg = qg;
     }
-    // the caller's stream resumes only after the last Q / Z update
-    if (qz && group >= 1 && cudaStreamWaitEvent(st, ctx->ev_qz[(group - 1) & 1], 0) != cudaSuccess)
+    if (lookahead) {
+        int last = group - 1;   // index of the last update launch
+        if (qz) {
+            // the closing launch: the last group's Q / Z update
+            UpdSched us;
+            us.P = task_plan(n, r, 1, 1, false, nqz);
+            us.tflags = P.tfl; us.epoch = (unsigned long long)(group + 1); us.ticket = P.tick + group;
+            us.status = status; us.group = group; us.n = n; us.r = r;
+            ProfScope ps(ctx, side);
+            if ((e = launch_update(ctx, emu, us, A, lda, B, ldb, qzM, qzld, qzkind, n, r, prev_j1, prev_qg, prev_set,
+                                   prev_j1, prev_qg, prev_set, q, P, side)) != cudaSuccess)
+                return HTS_ERR_CUDA;
+            ps.done(HTS_K_UPDATE, prev_gc.f_qz, prev_gc.b_qz, emu ? prev_gc.m_qz : 0.0);
+            if (cudaEventRecord(ctx->ev_upd[group % kSets], side) != cudaSuccess) return HTS_ERR_CUDA;
+            last = group;
+        }
+        if (last >= 0 && cudaStreamWaitEvent(st, ctx->ev_upd[last % kSets], 0) != cudaSuccess) return HTS_ERR_CUDA;
+    } else if (qz && group >= 1 && cudaStreamWaitEvent(st, ctx->ev_qz[(group - 1) % kSets], 0) != cudaSuccess) {
         return HTS_ERR_CUDA;
+    }
     if (!(flags & HTS_FLAG_NO_CLEAN)) {
         ProfScope ps(ctx, st);
-        if ((e = launch_zero_below(A, lda, n, 1, ctx->d_status, st)) != cudaSuccess) return HTS_ERR_CUDA;
-        if ((e = launch_zero_below(B, ldb, n, 0, ctx->d_status, st)) != cudaSuccess) return HTS_ERR_CUDA;
+        if ((e = launch_zero_below(A, lda, n, 1, status, st)) != cudaSuccess) return HTS_ERR_CUDA;
+        if ((e = launch_zero_below(B, ldb, n, 0, status, st)) != cudaSuccess) return HTS_ERR_CUDA;
         ps.done(HTS_K_UTIL, 0.0, 0.0);
     }
     return HTS_OK;
@@ -404,11 +511,14 @@ hts_status hts_create(hts_ctx **ctx, int device)
     bool ok = cudaMalloc(&c->d_status, kStatusWords * sizeof(int)) == cudaSuccess &&
               cudaMemset(c->d_status, 0, kStatusWords * sizeof(int)) == cudaSuccess &&
               cudaMallocHost(&c->h_status, kStatusWords * sizeof(int)) == cudaSuccess &&
+              cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
               cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) == cudaSuccess &&
-              cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, lo_prio) == cudaSuccess;
-    for (int b = 0; ok && b < 2; ++b)
+              cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, lo_prio) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&c->upd, cudaStreamNonBlocking, lo_prio) == cudaSuccess;
+    for (int b = 0; ok && b < 3; ++b)
         ok = cudaEventCreateWithFlags(&c->ev_gen[b], cudaEventDisableTiming) == cudaSuccess &&
-             cudaEventCreateWithFlags(&c->ev_qz[b], cudaEventDisableTiming) == cudaSuccess;
+             cudaEventCreateWithFlags(&c->ev_qz[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_upd[b], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         hts_destroy(c);
         return HTS_ERR_CUDA;
@@ -426,11 +536,14 @@ void hts_destroy(hts_ctx *ctx)
         hts_profile_end(ctx, tmp, nullptr);
     }
     if (ctx->side) cudaStreamSynchronize(ctx->side);
-    for (int b = 0; b < 2; ++b) {
+    if (ctx->upd) cudaStreamSynchronize(ctx->upd);
+    for (int b = 0; b < 3; ++b) {
         if (ctx->ev_gen[b]) cudaEventDestroy(ctx->ev_gen[b]);
         if (ctx->ev_qz[b]) cudaEventDestroy(ctx->ev_qz[b]);
+        if (ctx->ev_upd[b]) cudaEventDestroy(ctx->ev_upd[b]);
     }
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->upd) cudaStreamDestroy(ctx->upd);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     std::free(ctx);

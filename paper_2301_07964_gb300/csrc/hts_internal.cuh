@@ -24,11 +24,14 @@ struct hts_ctx {
     int *d_status;   // device status word: [0] code, [1..4] {pencil, group, k, j}
     int *h_status;   // pinned host mirror used by hts_sync_status
     hts_prof_state prof;
-    // Second stream for the Q / Z updates, which overlap the next group's chase, and the
-    // events that order it against the caller's stream (created once by hts_create).
-    cudaStream_t side;
-    cudaEvent_t ev_gen[2];   // reflector set s written (generate done)
-    cudaEvent_t ev_qz[2];    // reflector set s no longer read (Q / Z update done)
+    // Streams beside the caller's (created once by hts_create): `upd` carries the look-ahead
+    // update launches, `side` the Q / Z updates of the serial schedule; events order them
+    // against the caller's stream, one per reflector set.
+    cudaStream_t side, upd;
+    cudaEvent_t ev_gen[3];   // reflector set s written (generate and block formation done)
+    cudaEvent_t ev_qz[3];    // serial schedule: set s no longer read by its Q / Z update
+    cudaEvent_t ev_upd[3];   // look-ahead: update launch u (u mod 3) finished
+    int num_sms;
 };
 
 namespace hts {
@@ -168,6 +171,13 @@ __device__ __forceinline__ double warp_larfg(double xi, int m, int lane, double 
     return tau;
 }
 
+// Barrier of a group of nthreads threads: a whole block with id 0 (nthreads = its size), or
+// one worker of a persistent block with its own id.
+__device__ __forceinline__ void group_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // Brackets one kernel launch with profiler events when profiling is on (profile.cu).
 struct ProfScope {
     hts_ctx *ctx;
@@ -175,6 +185,25 @@ struct ProfScope {
     int idx;
     ProfScope(hts_ctx *c, cudaStream_t s);
     void done(int kind, double flops, double bytes, double mma_flops = 0.0);
+};
+
+constexpr int kTileLines = 32;   // lines per update task (rows of a right tile, columns of a left one)
+
+// Task layout of one update launch: the A / B updates of a group (if ab) and the Q / Z update of
+// the group before it (nqz matrices).  Tickets 0 .. 4U-1 form U slots {right A, right B, left A,
+// left B}: slot u holds right tile T0+u and left tiles Cs[m]+u-D[m], so that a left tile comes
+// after the right tiles it waits for.  Then the right tiles 0 .. T0-1 of A and B, then the Q / Z
+// tiles.
+struct TaskPlan {
+    int ntiles;     // tiles of 32 lines covering n
+    int ab;         // the launch carries a group's A / B updates
+    int T0, Tend;   // right tiles T0 .. Tend: rows below j1 that still need blocks of the group
+    int Cs[2], Ce;  // left tiles Cs[m] .. Ce of A (m = 0) and B (m = 1) with work
+    int D[2];       // slot lag of the left tiles
+    int U;          // slots
+    int nrect;      // right tiles above the group (A and B)
+    int nqz;        // matrices of the Q / Z update (0, 1 or 2)
+    int total;      // tasks
 };
 
 // Arguments of the stage-2 launches (kernels in stage2.cu).
@@ -192,6 +221,11 @@ struct GenArgs {
     int *status;
     int stall;                   // fault injection: slot 0 never publishes (tests only)
     int direct_rq;               // tests: the r <= 16 chase takes every direction from the RQ
+    // look-ahead: the previous group's update launch runs beside this chase; each step waits
+    // for the tiles of A and B it touches (uflags null: nothing to wait for)
+    const unsigned long long *uflags;
+    TaskPlan uplan;
+    unsigned long long uepoch;
 };
 
 // kind 0 = A, 1 = B (Z^ reflectors on rows x < i4(k, j)), 2 = Z (Z^, all rows),
@@ -227,6 +261,17 @@ struct EmuArgs {
     const int *status;
 };
 
+// Look-ahead update launch (schedule.cuh): the tasks of one group's A / B updates and of the
+// previous group's Q / Z update, the tile flags they publish and the launch's ticket counter.
+struct UpdSched {
+    TaskPlan P;
+    unsigned long long *tflags;   // 4 * P.ntiles words (see tile_flag)
+    unsigned long long epoch;     // published value: this group's index + 1
+    unsigned *ticket;
+    int *status;
+    int group, n, r;
+};
+
 struct LeftArgs {
     double *A;
     double *B;
@@ -243,6 +288,23 @@ cudaError_t launch_s2_emu_apply(const EmuArgs &a, int nmat, cudaStream_t st);
 size_t emu_plane_bytes(int kdim);
 bool emu_supported(int r, int qg);
 cudaError_t launch_s2_apply_right(const ApplyArgs &a, int nmat, cudaStream_t st);
+// Look-ahead update launches: `ab` carries A (M[0], kind 0 / 4) and B (M[1], kind 1 / 5) of the
+// group, `qz` the previous group's Q / Z; `ctas` persistent blocks.
+struct UpdEmuArgs {
+    EmuArgs right, left, qz;
+    UpdSched s;
+};
+cudaError_t launch_s2_update_emu(const UpdEmuArgs &a, int ctas, cudaStream_t st);
+struct UpdFp64Args {
+    ApplyArgs right, qz;
+    LeftArgs left;
+    UpdSched s;
+    int smem_doubles;   // shared memory of one worker
+};
+int update_fp64_smem_doubles(int r, int qg);
+int update_fp64_workers();
+int update_emu_workers();
+cudaError_t launch_s2_update_fp64(const UpdFp64Args &a, int ctas, cudaStream_t st);
 cudaError_t launch_s2_apply_left(const LeftArgs &a, cudaStream_t st);
 cudaError_t launch_set_identity(double *M, int ld, int n, cudaStream_t st);
 cudaError_t launch_zero_below(double *M, int ld, int n, int band, const int *status, cudaStream_t st);
@@ -299,14 +361,18 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
-// Bounded wait (one thread) until *flag >= need; on expiry records HTS_ERR_TIMEOUT.
+// Bounded wait (one thread) until *flag >= need; on expiry records HTS_ERR_TIMEOUT.  Gives up
+// at once (without recording) when another block has recorded an error, since the flag may
+// then never be set.
 __device__ __forceinline__ bool wait_at_least(const unsigned long long *flag, unsigned long long need, int *status, int group, int k,
                               int j)
 {
     const unsigned long long t0 = globaltimer_ns();
     long long polls = 0;
     while (ld_acquire_u64(flag) < need) {
-        if (++polls > kSpinLimit || globaltimer_ns() - t0 > kWaitLimitNs) {
+        ++polls;
+        if ((polls & 255) == 0 && *(volatile int *)status != 0) return false;
+        if (polls > kSpinLimit || globaltimer_ns() - t0 > kWaitLimitNs) {
             record_error(status, HTS_ERR_TIMEOUT, 0, group, k, j);
             return false;
         }

@@ -8,6 +8,8 @@
 // qg*r + qg doubles).  kind 0, 1 (A, B): reflector Z^_k^j applies to row x only while
 // x < i4(k, j), the rows the generate phase did not update; kind 2, 3 (Z, Q): all rows.
 // The next window's new columns are loaded into registers while the current window is updated.
+// tid is the thread's index in its group of NT threads and bar the id of that group's barrier
+// (0 for a whole block).
 #pragma once
 
 #include "hts_internal.cuh"
@@ -19,7 +21,7 @@ constexpr int kRightLanes = 4;
 template <int NT>
 __device__ __forceinline__ void right_window_rows(double *X, int ld, int kind, const double *Vs, const double *Ts,
                                                   int kdim, int n, int r, int j1, int qg, int x0, int kstart,
-                                                  int kstop, double *sm)
+                                                  int kstop, double *sm, int tid, int bar)
 {
     constexpr int NR = NT / kRightLanes;                    // rows per thread block
     constexpr int kPrefetch = kMaxR * NR / NT;              // new elements per thread
@@ -28,7 +30,6 @@ __device__ __forceinline__ void right_window_rows(double *X, int ld, int kind, c
     double *buf = sm;                       // [w][LDS]: row rr of the tile, window column p
     double *vr = buf + (size_t)w * LDS;     // [qg][r]
     double *tr = vr + (size_t)qg * r;       // [qg]
-    const int tid = threadIdx.x;
     const int rr = tid / kRightLanes, sub = tid % kRightLanes;
     const int x = x0 + rr;
 
@@ -59,7 +60,7 @@ __device__ __forceinline__ void right_window_rows(double *X, int ld, int kind, c
                 pre[t] = (p < r && xr <= n) ? X[AT(ld, xr, c)] : 0.0;
             }
         }
-        __syncthreads();
+        group_sync(bar, NT);
         for (int sidx = 0; sidx < qg; ++sidx) {
             const double tau = tr[sidx];
             if (tau == 0.0) continue;
@@ -77,7 +78,7 @@ __device__ __forceinline__ void right_window_rows(double *X, int ld, int kind, c
             if (active)
                 for (int i = sub; i < mlen; i += kRightLanes) b[i * LDS] -= d * v[i];
         }
-        __syncthreads();
+        group_sync(bar, NT);
         // store the columns that leave the window, keep the overlap, insert the prefetch
         const int plo = (k > kstop) ? qg - 1 : 0;
         const int np = w - plo;
@@ -87,19 +88,19 @@ __device__ __forceinline__ void right_window_rows(double *X, int ld, int kind, c
             if (c <= n && xr <= n) X[AT(ld, xr, c)] = buf[p * LDS + re];
         }
         if (k > kstop) {
-            __syncthreads();
+            group_sync(bar, NT);
             for (int e = tid; e < (qg - 1) * NR; e += NT) {
                 const int p = e / NR, re = e % NR;
                 buf[(p + r) * LDS + re] = buf[p * LDS + re];
             }
-            __syncthreads();
+            group_sync(bar, NT);
 #pragma unroll
             for (int t = 0; t < kPrefetch; ++t) {
                 const int e = tid + t * NT;
                 const int p = e / NR, re = e % NR;
                 if (p < r) buf[p * LDS + re] = pre[t];
             }
-            __syncthreads();
+            group_sync(bar, NT);
         }
     }
 }

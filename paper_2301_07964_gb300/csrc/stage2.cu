@@ -12,6 +12,7 @@
 // r + qg - 1 columns (rows), so every element is read and written once per group; inside
 // the window the group's reflectors are applied one at a time in FP64.
 #include "right_window.cuh"
+#include "schedule.cuh"
 
 namespace hts {
 
@@ -21,18 +22,17 @@ namespace hts {
 // updated the rest), 2 = Z (Z^ reflectors, all rows), 3 = Q (Q^ reflectors, all rows).
 // ---------------------------------------------------------------------------------------
 
+// One tile of rows (tile*NR+1 .., NR = NT/4) of matrix a.M[mi], by NT threads of a group with
+// barrier id bar.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_s2_apply_right(ApplyArgs a)
+__device__ __forceinline__ void right_tile_fp64(const ApplyArgs &a, int mi, int tile, double *sm, int tid, int bar)
 {
-    extern __shared__ double sm[];
-    constexpr int NR = NT / kRightLanes;                    // rows per thread block
+    constexpr int NR = NT / kRightLanes;                    // rows per tile
     const int n = a.n, r = a.r, j1 = a.j1, qg = a.qg;
-    const int mi = blockIdx.y;
     const int kind = a.kind[mi];
-    const int x0 = blockIdx.x * NR + 1;
+    const int x0 = tile * NR + 1;
     const int kmax = nblocks_gen(n, r, j1) - 1;
-
-    if (__ldcg(a.status) != 0) return;
+    if (x0 > n) return;
     int kstop = 0;
     if (kind <= 1) {
         // rows x0.. need block k only while x0 < i4(k, j1+qg-1) = j1 + 1 + max(0, (k-1) r)
@@ -40,7 +40,15 @@ __global__ void __launch_bounds__(NT) k_s2_apply_right(ApplyArgs a)
         if (kstop > kmax) return;
     }
     right_window_rows<NT>(a.M[mi], a.ld[mi], kind, (kind == 3) ? a.R.VQ : a.R.VZ, (kind == 3) ? a.R.TQ : a.R.TZ,
-                          a.R.kdim, n, r, j1, qg, x0, kmax, kstop, sm);
+                          a.R.kdim, n, r, j1, qg, x0, kmax, kstop, sm, tid, bar);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_s2_apply_right(ApplyArgs a)
+{
+    extern __shared__ double sm[];
+    if (__ldcg(a.status) != 0) return;
+    right_tile_fp64<NT>(a, blockIdx.y, blockIdx.x, sm, threadIdx.x, 0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -59,9 +67,10 @@ constexpr int kLeftThreads = 128;
 constexpr int kLeftLanes = 4;
 constexpr int kLeftCols = kLeftThreads / kLeftLanes;   // columns per thread block
 
-__global__ void __launch_bounds__(kLeftThreads) k_s2_apply_left(LeftArgs a)
+// One column tile (columns ctile*kLeftCols+1 ..) of the left update of A (isB = 0) or B, by
+// the kLeftThreads threads tid of a group whose barrier is bar (0: a whole block).
+__device__ __forceinline__ void left_tile(const LeftArgs &a, int isB, int ctile, double *sm, int tid, int bar)
 {
-    extern __shared__ double sm[];
     const int NT = kLeftThreads;
     const int NC = kLeftCols;
     const int LDS = NC + 1;
@@ -71,26 +80,23 @@ __global__ void __launch_bounds__(kLeftThreads) k_s2_apply_left(LeftArgs a)
     double *buf = sm;                       // [w][LDS]: column cc of the tile at buf[p*LDS+cc]
     double *vr = buf + (size_t)w * LDS;     // [qg][r]
     double *tr = vr + (size_t)qg * r;       // [qg]
-    const int isB = blockIdx.y;
     double *X = isB ? a.B : a.A;
     const int ld = isB ? a.ldb : a.lda;
-    const int tid = threadIdx.x;
     const int cc = tid / kLeftLanes, sub = tid % kLeftLanes;
-    const int cbase = (gridDim.x - 1 - blockIdx.x) * NC + 1;   // rightmost tiles carry most work
+    const int cbase = ctile * NC + 1;
     const int c = cbase + cc;
     const int clast = imin(cbase + NC - 1, n);
     const int kdim = a.R.kdim;
     const int kmax = nblocks_gen(n, r, j1) - 1;
 
-    if (__ldcg(a.status) != 0) return;
     int ktop = -1;
     for (int k = kmax; k >= 0; --k)
         if (left_cut(isB, n, r, jl, k) < clast) { ktop = k; break; }
-    if (ktop < 0) return;
+    if (ktop < 0 || cbase > n) return;
 
     for (int k = ktop; k >= 0; --k) {
         const int R0 = j1 + k * r + 1;
-        __syncthreads();
+        group_sync(bar, NT);
         for (int e = tid; e < qg * r; e += NT) {
             const int sidx = e / r, i = e % r;
             vr[e] = a.R.VQ[((size_t)sidx * kdim + k) * r + i];
@@ -102,7 +108,7 @@ __global__ void __launch_bounds__(kLeftThreads) k_s2_apply_left(LeftArgs a)
             const int row = R0 + p, colx = cbase + ce;
             if (row <= n && colx <= n) buf[p * LDS + ce] = X[AT(ld, row, colx)];
         }
-        __syncthreads();
+        group_sync(bar, NT);
         const bool active = c <= n && c > left_cut(isB, n, r, jl, k);
         for (int sidx = 0; sidx < qg; ++sidx) {
             const double tau = tr[sidx];
@@ -119,7 +125,7 @@ __global__ void __launch_bounds__(kLeftThreads) k_s2_apply_left(LeftArgs a)
             if (active)
                 for (int i = sub; i < mlen; i += kLeftLanes) b[i * LDS] -= d * v[i];
         }
-        __syncthreads();
+        group_sync(bar, NT);
         const int plo = (k > 0) ? qg - 1 : 0;
         const int np = w - plo;
         for (int e = tid; e < np * NC; e += NT) {
@@ -127,13 +133,42 @@ __global__ void __launch_bounds__(kLeftThreads) k_s2_apply_left(LeftArgs a)
             const int row = R0 + p, colx = cbase + ce;
             if (row <= n && colx <= n) X[AT(ld, row, colx)] = buf[p * LDS + ce];
         }
-        __syncthreads();
+        group_sync(bar, NT);
         if (k > 0)
             for (int e = tid; e < (qg - 1) * NC; e += NT) {
                 const int p = e / NC, ce = e % NC;
                 buf[(p + r) * LDS + ce] = buf[p * LDS + ce];
             }
     }
+}
+
+__global__ void __launch_bounds__(kLeftThreads) k_s2_apply_left(LeftArgs a)
+{
+    extern __shared__ double sm[];
+    if (__ldcg(a.status) != 0) return;
+    // the rightmost tiles carry the most work: they start first
+    left_tile(a, blockIdx.y, gridDim.x - 1 - blockIdx.x, sm, threadIdx.x, 0);
+}
+
+// ---------------------------------------------------------------------------------------
+// Look-ahead update launch in native FP64 (schedule.cuh): one block per SM with kUpdFp64Workers
+// workers of 128 threads (barrier id w+1), each with its own slice of shared memory.
+// ---------------------------------------------------------------------------------------
+constexpr int kUpdFp64Workers = 4;
+constexpr int kUpdThreads = 128;
+
+__global__ void __launch_bounds__(kUpdThreads * kUpdFp64Workers, 1) k_s2_update_fp64(UpdFp64Args a)
+{
+    extern __shared__ double upd_sm[];
+    __shared__ int slot[kUpdFp64Workers];
+    const int worker = threadIdx.x / kUpdThreads, tid = threadIdx.x % kUpdThreads;
+    double *sm = upd_sm + (size_t)worker * a.smem_doubles;
+    const int wb = 1 + worker;
+    update_worker<kUpdThreads>(a.s, tid, wb, &slot[worker], [&](const Task &T) {
+        if (T.kind == kTaskRight) right_tile_fp64<kUpdThreads>(a.right, T.mat, T.tile, sm, tid, wb);
+        else if (T.kind == kTaskLeft) left_tile(a.left, T.mat, T.tile, sm, tid, wb);
+        else if (T.kind == kTaskQZ) right_tile_fp64<kUpdThreads>(a.qz, T.mat, T.tile, sm, tid, wb);
+    });
 }
 
 // ---------------------------------------------------------------------------------------
@@ -212,6 +247,29 @@ cudaError_t launch_s2_apply_left(const LeftArgs &a, cudaStream_t st)
     if (e != cudaSuccess) return e;
     dim3 grid((a.n + kLeftCols - 1) / kLeftCols, 2);
     k_s2_apply_left<<<grid, kLeftThreads, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+int update_fp64_workers() { return kUpdFp64Workers; }
+
+// Shared memory of one native update worker, in doubles (a multiple of 2, so that every
+// worker's slice stays 16-byte aligned).
+int update_fp64_smem_doubles(int r, int qg)
+{
+    const size_t b = apply_right_smem(r, qg, kUpdThreads / kRightLanes);
+    const size_t l = apply_left_smem(r, qg);
+    const size_t d = (b > l ? b : l) / sizeof(double);
+    return (int)((d + 1) & ~(size_t)1);
+}
+
+cudaError_t launch_s2_update_fp64(const UpdFp64Args &a, int ctas, cudaStream_t st)
+{
+    // at least 116 KiB, so that two blocks never share an SM and the free SMs stay whole
+    size_t sm = (size_t)kUpdFp64Workers * a.smem_doubles * sizeof(double);
+    if (sm < 116 * 1024) sm = 116 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_s2_update_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_s2_update_fp64<<<ctas, kUpdThreads * kUpdFp64Workers, sm, st>>>(a);
     return cudaGetLastError();
 }
 

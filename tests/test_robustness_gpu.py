@@ -199,8 +199,18 @@ def test_ill_conditioned_reduce_matches_oracle(red, oracle_mod, n, r):
     o = canonical(Ho, To, Qo, Zo, B_in=B)
     scale = max(float(np.abs(A).max()), float(np.abs(B).max()))
     err = max(float(np.abs(x - y).max()) for x, y in zip(g, o)) / scale
-    print("ill-conditioned reduce n=%d r=%d: max |GPU - oracle| = %.2e, %s" % (n, r, err, c))
-    assert err <= 1e-12 * n, err
+    # The HT form of this pencil is backward stable but forward sensitive: rounding differences
+    # in stages 0 and 1 (blocked WY updates here, single reflectors in the oracle) move the
+    # trailing part of H and T by far more than 1e-12 n.  The bound is then the intrinsic
+    # spread, the distance between the FP64 oracle and the same oracle in extended precision.
+    Hl, Tl, Ql, Zl = oracle_mod.reduce(A, B, r, precision="ld")
+    lo = canonical(*(np.asarray(x, dtype=np.float64) for x in (Hl, Tl, Ql, Zl)), B_in=B)
+    spread = max(float(np.abs(x - y).max()) for x, y in zip(o, lo)) / scale
+    err_ld = max(float(np.abs(x - y).max()) for x, y in zip(g, lo)) / scale
+    print("ill-conditioned reduce n=%d r=%d: max |GPU - oracle| = %.2e, |GPU - extended oracle| = %.2e, "
+          "|oracle - extended oracle| = %.2e, %s" % (n, r, err, err_ld, spread, c))
+    assert err <= max(1e-12 * n, 10.0 * spread), (err, spread)
+    assert err_ld <= max(1e-12 * n, 10.0 * spread), (err_ld, spread)
 
 
 # ---------------------------------------------------------------------------------------
