@@ -297,6 +297,7 @@ def run_ours(args, n, r):
 
     q = args.q or r
     mode = b.HTS_GEMM_FP64 if args.mode == "fp64" else b.HTS_GEMM_EMU_BF16
+    sched_flags = b.HTS_FLAG_SERIAL_UPDATES if args.serial else 0
     A, B = random_rht_pencil(n, r, SEED)
     dA0, dB0 = to_device(A), to_device(B)
     dA, dB = colmajor_empty(n), colmajor_empty(n)
@@ -312,7 +313,7 @@ def run_ours(args, n, r):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, mode=mode,
-                   stream=stream)
+                   flags=sched_flags, stream=stream)
         e1.record(stream)
         return e0, e1
 
@@ -379,7 +380,7 @@ def run_ours(args, n, r):
             dA.t().copy_(hA, non_blocking=True)
             dB.t().copy_(hB, non_blocking=True)
             red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, mode=mode,
-                       stream=stream)
+                       flags=sched_flags, stream=stream)
             for o, d in zip(outs, (dA, dB, dQ, dZ)):
                 o.copy_(d.t(), non_blocking=True)
             torch.cuda.synchronize()
@@ -435,6 +436,7 @@ def run_ours(args, n, r):
         "config": {"workload": "stage 2, n=%d r=%d q=%d, seeded r-HT pencil (A band iid N(0,1), B = R of "
                                "a Gaussian), Q and Z accumulated, delayed updates %s" % (n, r, q, args.mode),
                    "n": n, "r": r, "q": q, "mode": args.mode, "parallelism": "replicas" if ws > 1 else "single",
+                   "schedule": "serial" if args.serial else "look-ahead",
                    "l2": "inputs (A, B: %.1f GiB) larger than L2" % (2 * 8 * n * n / 2 ** 30)},
         "backward_error": bwd,
         "direct_gflops": ws * 8.0 * n ** 3 / (ms / 1e3) / 1e9,
@@ -615,6 +617,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--r", type=int, default=R_DEFAULT)
     ap.add_argument("--q", type=int, default=0)
+    ap.add_argument("--serial", action="store_true",
+                    help="stage 2: each group's delayed updates after its chase (no look-ahead)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

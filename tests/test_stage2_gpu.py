@@ -224,3 +224,32 @@ def test_full_size_properties(red, n, r, q, seed):
     assert p["Qe1"] and p["Ze1"], p
     for key in ("bwd_A", "bwd_B", "orth_Q", "orth_Z"):
         assert p[key] < 1e-12 * n, p
+
+
+@pytest.mark.parametrize("n,r,q,mode", [(300, 16, 16, b.HTS_GEMM_FP64), (300, 16, 16, b.HTS_GEMM_EMU_BF16),
+                                        (301, 32, 13, b.HTS_GEMM_FP64), (129, 8, 5, b.HTS_GEMM_FP64),
+                                        (700, 16, 16, b.HTS_GEMM_EMU_BF16), (517, 16, 9, b.HTS_GEMM_EMU_BF16),
+                                        (97, 4, 3, b.HTS_GEMM_FP64)])
+def test_lookahead_and_serial_schedules_match_oracle(red, oracle_mod, n, r, q, mode):
+    """The default schedule runs group g's delayed updates beside group g+1's chase (each chase
+    step waits for the update tiles it touches); HTS_FLAG_SERIAL_UPDATES runs them after the
+    chase.  Both must give the oracle's reduction, and agree with each other."""
+    from paper_2301_07964_gb300.device import colmajor_empty, to_device, to_host
+    A, B = random_rht_pencil(n, r, 5000 * n + 10 * r + q)
+    res = []
+    for flags in (0, b.HTS_FLAG_SERIAL_UPDATES):
+        dA, dB = to_device(A), to_device(B)
+        dQ, dZ = colmajor_empty(n), colmajor_empty(n)
+        red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, flags=flags, mode=mode)
+        st, info = red.sync_status()
+        assert st == b.HTS_OK, (b.status_string(st), info)
+        H, T, Q, Z = (to_host(x) for x in (dA, dB, dQ, dZ))
+        c = rht_pencil_checks(A, B, H, T, Q, Z)
+        assert c["H_below_hessenberg"] == 0.0 and c["T_below_diag"] == 0.0, c
+        for key in ("bwd_A", "bwd_B", "orth_Q", "orth_Z"):
+            assert c[key] < 1e-14 * max(n, 10), c
+        err, tol = _compare(oracle_mod, A, B, r, H, T, Q, Z)
+        assert err <= tol, (flags, err, tol)
+        res.append(canonical(H, T, Q, Z))
+    scale = max(1.0, float(np.abs(A).max()), float(np.abs(B).max()))
+    assert max(float(np.abs(x - y).max()) for x, y in zip(*res)) / scale <= 1e-12 * n
