@@ -162,8 +162,7 @@ hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r,
  *    the library holds it until the process exits.  A call whose stage-2 scratch in the chosen
  *    update mode exceeds 8 MiB is rejected with HTS_ERR_WORKSPACE before anything runs (the
  *    check precedes every other argument check).  In native FP64 mode r = 16 fits n up to
- *    about 9000; the emulated mode's digit planes (64 KiB per block of r columns) fit only
- *    small n (about 500 at r = 16).
+ *    6943 and r = 32 up to 5215; the emulated mode's digit planes fit n up to 1119 at r = 16.
  *  - The call allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  *    with that device current); make that first call before any stream capture.
