@@ -24,106 +24,18 @@
 // 2^(e-58) for typical digits (2^(e-53) for adversarial ones), far below one FP64 rounding unit
 // of the window's largest entry.  No FP64 instruction runs in the update loop: FP64 values enter and leave
 // through integer bit manipulation of their IEEE-754 encoding.
+#include "emu_arith.cuh"
 #include "right_window.cuh"
 #include "schedule.cuh"
 
 namespace hts {
 
+using namespace emu;
+
 namespace {
 
-constexpr int kDigits = 8;                 // balanced base-256 digits per operand
-constexpr int kTopLevel = 9;               // digit pairs with i + t <= 9 are formed
-constexpr int kPlaneWords = kDigits * 2 * 4 * 32;   // uint2 words of one U_k (16 KiB)
-constexpr int kUnitU = -61;                // U_k entries as integers round(u 2^61)
 constexpr int kEmuWarps = 2;               // 16-line slabs per apply block
 constexpr int kEmuRows = 16 * kEmuWarps;   // rows (or columns) per apply block
-constexpr int kZeroExp = -4000;            // "exponent" of a zero value
-
-// ---- IEEE-754 double <-> fixed point (integer arithmetic only) --------------------------
-
-// Smallest e with |v| < 2^e, or kZeroExp for zero and subnormal v (treated as zero).
-__device__ __forceinline__ int exp_of_f64(double v)
-{
-    const int eb = (int)((__double_as_longlong(v) >> 52) & 0x7ff);
-    return eb == 0 ? kZeroExp : eb - 1022;
-}
-
-// Smallest e with |x 2^unit| < 2^e, or kZeroExp.
-__device__ __forceinline__ int exp_of_fixed(long long x, int unit)
-{
-    if (x == 0) return kZeroExp;
-    const unsigned long long m = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
-    return 64 - __clzll(m) + unit;
-}
-
-// round(v 2^-unit) for |v| < 2^(unit + 62); zero and subnormal v give 0.
-__device__ __forceinline__ long long f64_to_fixed(double v, int unit)
-{
-    const long long b = __double_as_longlong(v);
-    const int eb = (int)((b >> 52) & 0x7ff);
-    if (eb == 0) return 0;
-    const long long mant = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;   // v = +-mant 2^(eb-1075)
-    const int sh = eb - 1075 - unit;
-    long long x;
-    if (sh >= 0) x = mant << sh;
-    else if (sh > -63) x = (mant + (1LL << (-sh - 1))) >> (-sh);
-    else x = 0;
-    return b < 0 ? -x : x;
-}
-
-// x 2^unit rounded to the nearest double (ties to even); results below the normal range
-// become signed zero.
-__device__ __forceinline__ double fixed_to_f64(long long x, int unit)
-{
-    if (x == 0) return 0.0;
-    const unsigned long long sgn = x < 0 ? 0x8000000000000000ULL : 0ULL;
-    unsigned long long m = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
-    const int lz = __clzll(m);
-    m <<= lz;                                    // leading one at bit 63
-    const int eb = 63 - lz + unit + 1023;        // biased exponent of the result
-    if (eb <= 0) return __longlong_as_double((long long)sgn);
-    unsigned long long mant = m >> 11;           // 53 bits including the leading one
-    const unsigned long long rem = m & 0x7ffULL;
-    if (rem > 0x400ULL || (rem == 0x400ULL && (mant & 1ULL))) ++mant;
-    // the leading one of mant adds 1 to the exponent field; a rounding carry adds one more
-    const unsigned long long bits = ((unsigned long long)(eb - 1) << 52) + mant;
-    return __longlong_as_double((long long)(sgn | bits));
-}
-
-// x 2^su expressed in units 2^du (rounded), for values known to fit.
-__device__ __forceinline__ long long refix(long long x, int su, int du)
-{
-    const int s = su - du;
-    if (s >= 0) return x << s;
-    if (s > -63) return (x + (1LL << (-s - 1))) >> (-s);
-    return 0;
-}
-
-// ---- balanced digits --------------------------------------------------------------------
-
-// BF16 bit patterns of the 8 balanced base-256 digits of x (|x| < 2^62), most significant
-// first, in the upper halves of FP32 words: with u = x + 0x8080808080808080 (no wrap-around
-// in that range), digit i is byte (8 - i) of u minus 128.  One byte permute places the byte
-// under the exponent of 2^23 and one subtraction removes 2^23 + 128; a digit in [-128, 127]
-// has 16 trailing zero bits in FP32, so the upper half of its encoding is its exact BF16.
-__device__ __forceinline__ void digits_bf16(long long x, unsigned (&bf)[kDigits])
-{
-    const unsigned long long u = (unsigned long long)x + 0x8080808080808080ULL;
-    const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
-#pragma unroll
-    for (int i = 0; i < kDigits; ++i) {
-        const unsigned word = (i < 4) ? hi : lo;
-        const unsigned sel = 0x7650u | (unsigned)(3 - (i & 3));   // bytes {b, 0, 0, 0x4B}
-        bf[i] = __float_as_uint(__uint_as_float(__byte_perm(word, 0x4B000000u, sel)) - 8388736.0f);
-    }
-}
-
-// Two BF16 values (the upper halves of the FP32 words lo and hi) in one register, lo in the
-// low half.
-__device__ __forceinline__ unsigned pack_bf16(unsigned lo, unsigned hi) { return __byte_perm(lo, hi, 0x7632u); }
-
-// An FP32 value holding an integer of magnitude below 2^22, as int (exact).
-__device__ __forceinline__ int f32_exact_int(float c) { return __float_as_int(c + 12582912.0f) - 0x4B400000; }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
 {

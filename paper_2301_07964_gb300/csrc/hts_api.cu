@@ -58,7 +58,7 @@ S2Layout s2_layout(int n, int r)
         if (r <= 16) o = align_up(o + (size_t)L.kdim * L.qmax * L.qmax * sizeof(double), 256);
     }
     L.off_flags = o; o = align_up(o + 2 * (size_t)L.qmax * sizeof(unsigned long long), 256);
-    L.ntiles = (n + kTileLines - 1) / kTileLines;
+    L.ntiles = (n + 31) / 32;   // tiles of the smallest tile height (32 lines)
     L.off_tflags = o; o = align_up(o + 4 * (size_t)L.ntiles * sizeof(unsigned long long), 256);
     L.nticket = n + 2;   // one per update launch: at most n - 2 groups plus the closing Q / Z launch
     L.off_tick = o; o = align_up(o + (size_t)L.nticket * sizeof(unsigned), 256);
@@ -344,7 +344,7 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
     cudaStream_t side = lookahead ? ctx->upd : ctx->side;
 
     int group = 0, prev_set = 0, prev_j1 = 0, prev_qg = 0;
-    TaskPlan prev_plan = task_plan(n, r, 1, 1, false, 0);
+    TaskPlan prev_plan = task_plan(n, r, 1, 1, false, 0, 32);
     GroupCost prev_gc{};
     for (int j1 = 1; j1 <= n - 2; j1 += q, ++group) {
         const int qg = imin(q, n - 2 - j1 + 1);
@@ -389,7 +389,7 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
             if (cudaStreamWaitEvent(side, ctx->ev_gen[set], 0) != cudaSuccess) return HTS_ERR_CUDA;
             const int nq = group >= 1 ? nqz : 0;
             UpdSched us;
-            us.P = task_plan(n, r, j1, qg, true, nq);
+            us.P = task_plan(n, r, j1, qg, true, nq, 32);
             us.tflags = P.tfl; us.epoch = (unsigned long long)(group + 1); us.ticket = P.tick + group;
             us.status = status; us.group = group; us.n = n; us.r = r;
             ProfScope ps(ctx, side);
@@ -452,7 +452,7 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         if (qz) {
             // the closing launch: the last group's Q / Z update
             UpdSched us;
-            us.P = task_plan(n, r, 1, 1, false, nqz);
+            us.P = task_plan(n, r, 1, 1, false, nqz, 32);
             us.tflags = P.tfl; us.epoch = (unsigned long long)(group + 1); us.ticket = P.tick + group;
             us.status = status; us.group = group; us.n = n; us.r = r;
             ProfScope ps(ctx, side);

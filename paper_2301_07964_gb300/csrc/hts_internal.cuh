@@ -187,7 +187,6 @@ struct ProfScope {
     void done(int kind, double flops, double bytes, double mma_flops = 0.0);
 };
 
-constexpr int kTileLines = 32;   // lines per update task (rows of a right tile, columns of a left one)
 
 // Task layout of one update launch: the A / B updates of a group (if ab) and the Q / Z update of
 // the group before it (nqz matrices).  Tickets 0 .. 4U-1 form U slots {right A, right B, left A,
@@ -195,7 +194,8 @@ constexpr int kTileLines = 32;   // lines per update task (rows of a right tile,
 // after the right tiles it waits for.  Then the right tiles 0 .. T0-1 of A and B, then the Q / Z
 // tiles.
 struct TaskPlan {
-    int ntiles;     // tiles of 32 lines covering n
+    int TL;         // lines per tile (rows of a right tile, columns of a left one)
+    int ntiles;     // tiles of TL lines covering n
     int ab;         // the launch carries a group's A / B updates
     int T0, Tend;   // right tiles T0 .. Tend: rows below j1 that still need blocks of the group
     int Cs[2], Ce;  // left tiles Cs[m] .. Ce of A (m = 0) and B (m = 1) with work

@@ -3,10 +3,10 @@
 //
 // The delayed updates of group g (Alg. 4) run as one persistent launch whose workers take
 // tasks in ticket order, while the chase of group g+1 (Alg. 3) runs beside it.  A task is one
-// tile of 32 lines:
-//   right tile T of A or B   rows 32T+1 .. 32T+32, every block k the rows still need (the
+// tile of TL lines (32 for the mma.sync kernel, 128 for the tcgen05 kernel):
+//   right tile T of A or B   rows TL T+1 .. TL T+TL, every block k the rows still need (the
 //                            windows from the last block to the first, then the staircase);
-//   left tile C of A or B    columns 32C+1 .. 32C+32, blocks from the lowest one whose cut lies
+//   left tile C of A or B    columns TL C+1 .. TL C+TL, blocks from the lowest one whose cut lies
 //                            left of the tile up to block 0;
 //   Q / Z tile of the previous group (g-1), all blocks.
 // A right tile and a left tile of the same matrix share elements, and the right update of each
@@ -39,27 +39,28 @@ __host__ __device__ __forceinline__ int left_cut_of(int isB, int n, int r, int j
     return isB ? imin(jl + (k + 1) * r, n) : jl + imax(0, (k - 1) * r + 1);
 }
 
-__host__ __device__ inline TaskPlan task_plan(int n, int r, int j1, int qg, bool ab, int nqz)
+__host__ __device__ inline TaskPlan task_plan(int n, int r, int j1, int qg, bool ab, int nqz, int TL)
 {
     TaskPlan P;
-    P.ntiles = (n + kTileLines - 1) / kTileLines;
+    P.TL = TL;
+    P.ntiles = (n + TL - 1) / TL;
     P.ab = ab ? 1 : 0;
     P.T0 = 0; P.Tend = -1; P.Cs[0] = P.Cs[1] = 0; P.Ce = -1; P.D[0] = P.D[1] = 0;
     P.U = 0; P.nrect = 0; P.nqz = nqz;
     if (ab) {
         const int kmax = nblocks_gen(n, r, j1) - 1;
         const int jl = j1 + qg - 1;
-        P.T0 = j1 / kTileLines;
+        P.T0 = j1 / TL;
         // a right tile needs blocks while its first row l0 <= j1 + max(0, kmax-1) r
         const int lmax = j1 + imax(0, kmax - 1) * r;
-        P.Tend = imin(P.ntiles - 1, (lmax - 1) / kTileLines);
+        P.Tend = imin(P.ntiles - 1, (lmax - 1) / TL);
         P.Ce = P.ntiles - 1;
         int U = P.Tend - P.T0 + 1;
         for (int m = 0; m < 2; ++m) {
             const int cut0 = left_cut_of(m, n, r, jl, 0);
-            P.Cs[m] = cut0 >= n ? P.ntiles : cut0 / kTileLines;
-            // a left tile C reaches rows <= 32(C+1) + 2r - 1 (A) or <= 32(C+1) (B)
-            P.D[m] = P.Cs[m] - P.T0 + (m == 0 ? 1 + (2 * r - 1) / kTileLines : 0);
+            P.Cs[m] = cut0 >= n ? P.ntiles : cut0 / TL;
+            // a left tile C reaches rows <= TL(C+1) + 2r - 1 (A) or <= TL(C+1) (B)
+            P.D[m] = P.Cs[m] - P.T0 + (m == 0 ? 1 + (2 * r - 1) / TL : 0);
             if (P.Cs[m] <= P.Ce) U = imax(U, P.Ce - P.Cs[m] + P.D[m] + 1);
         }
         P.U = imax(U, 0);
@@ -98,17 +99,17 @@ __host__ __device__ __forceinline__ size_t tile_flag(int ntiles, int kind, int m
 // Last right tile of matrix `mat` a left tile C waits for.
 __host__ __device__ __forceinline__ int left_dep_tile(const TaskPlan &P, int n, int r, int mat, int C)
 {
-    const int clast = imin((C + 1) * kTileLines, n);
+    const int clast = imin((C + 1) * P.TL, n);
     const int rmax = imin(n, clast + (mat == 0 ? 2 * r - 1 : 0));
-    return imin(P.Tend, (rmax - 1) / kTileLines);
+    return imin(P.Tend, (rmax - 1) / P.TL);
 }
 
 // Last tiles a chase step that touches rows <= i3 and columns <= i2 waits for: right tiles
 // T0 .. *nr and left tiles Cs[m] .. *nl.
 __host__ __device__ __forceinline__ void upd_wait_range(const TaskPlan &P, int n, int i2, int i3, int *nr, int *nl)
 {
-    *nr = imin(P.Tend, (imin(i3, n) - 1) / kTileLines);
-    *nl = imin(P.Ce, (imin(i2, n) - 1) / kTileLines);
+    *nr = imin(P.Tend, (imin(i3, n) - 1) / P.TL);
+    *nl = imin(P.Ce, (imin(i2, n) - 1) / P.TL);
 }
 
 // Progress of one chase block through the previous group's update tiles (used by one thread).

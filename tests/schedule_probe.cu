@@ -11,10 +11,10 @@ using namespace hts;
 
 int main(int argc, char **argv)
 {
-    if (argc < 7) return 2;
+    if (argc < 8) return 2;
     const int n = atoi(argv[1]), r = atoi(argv[2]), j1 = atoi(argv[3]), qg = atoi(argv[4]);
-    const int ab = atoi(argv[5]), nqz = atoi(argv[6]);
-    const TaskPlan P = task_plan(n, r, j1, qg, ab != 0, nqz);
+    const int ab = atoi(argv[5]), nqz = atoi(argv[6]), TL = atoi(argv[7]);
+    const TaskPlan P = task_plan(n, r, j1, qg, ab != 0, nqz, TL);
     printf("plan %d %d %d %d %d %d %d %d %d %d %d %d\n", P.ntiles, P.ab, P.T0, P.Tend, P.Cs[0], P.Cs[1], P.Ce,
            P.D[0], P.D[1], P.U, P.nrect, P.total);
     for (int t = 0; t < P.total; ++t) {

@@ -24,7 +24,6 @@ import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-TL = 32
 
 
 @pytest.fixture(scope="module")
@@ -38,8 +37,8 @@ def probe(tmp_path_factory):
     return exe
 
 
-def run_probe(exe, n, r, j1, qg, ab=1, nqz=2):
-    out = subprocess.run([exe, str(n), str(r), str(j1), str(qg), str(ab), str(nqz)], check=True,
+def run_probe(exe, n, r, j1, qg, TL, ab=1, nqz=2):
+    out = subprocess.run([exe, str(n), str(r), str(j1), str(qg), str(ab), str(nqz), str(TL)], check=True,
                          capture_output=True, text=True).stdout.split("\n")
     plan, tasks, waits = None, [], {}
     for line in out:
@@ -74,7 +73,7 @@ def left_cut(isB, n, r, jl, k):
     return min(jl + (k + 1) * r, n) if isB else jl + max(0, (k - 1) * r + 1)
 
 
-def right_tile_cols(n, r, j1, T):
+def right_tile_cols(n, r, j1, T, TL):
     """First column a right tile of group j1 writes (None: the tile has no work)."""
     kmax = nblocks_gen(n, r, j1) - 1
     l0 = T * TL + 1
@@ -86,7 +85,7 @@ def right_tile_cols(n, r, j1, T):
     return j1 + kstop * r + 1
 
 
-def left_tile_rows(n, r, j1, qg, m, C):
+def left_tile_rows(n, r, j1, qg, m, C, TL):
     """Last row a left tile of group j1 writes (None: no work); rows start at j1 + 1."""
     kmax = nblocks_gen(n, r, j1) - 1
     jl = j1 + qg - 1
@@ -121,12 +120,13 @@ CASES = [(200, 16, 16), (300, 16, 7), (257, 8, 8), (129, 4, 3), (400, 32, 32), (
          (64, 3, 2), (1000, 16, 16)]
 
 
+@pytest.mark.parametrize("TL", [32, 128])
 @pytest.mark.parametrize("n,r,q", CASES)
-def test_schedule_covers_and_orders(probe, n, r, q):
+def test_schedule_covers_and_orders(probe, n, r, q, TL):
     groups = list(range(1, n - 1, q))
     for gi, j1 in enumerate(groups[:-1]):
         qg = min(q, n - 2 - j1 + 1)
-        P, tasks, waits = run_probe(probe, n, r, j1, qg)
+        P, tasks, waits = run_probe(probe, n, r, j1, qg, TL)
         ticket = {}
         for t, kind, mat, tile, dep in tasks:
             if kind == 0:
@@ -138,12 +138,12 @@ def test_schedule_covers_and_orders(probe, n, r, q):
         nt = P["ntiles"]
         for m in (0, 1):
             for T in range(nt):
-                has = right_tile_cols(n, r, j1, T) is not None
+                has = right_tile_cols(n, r, j1, T, TL) is not None
                 assert ((1, m, T) in ticket) == has, ("right tile", m, T, has)
                 if has and T < P["T0"]:
                     assert (T + 1) * TL <= j1    # the rows above the group
             for C in range(nt):
-                has = left_tile_rows(n, r, j1, qg, m, C) is not None
+                has = left_tile_rows(n, r, j1, qg, m, C, TL) is not None
                 assert ((2, m, C) in ticket) == has, ("left tile", m, C, has)
         for m in (0, 1):
             for T in range(nt):
@@ -152,9 +152,9 @@ def test_schedule_covers_and_orders(probe, n, r, q):
         for (kind, m, C), (t, dep) in ticket.items():
             if kind != 2:
                 continue
-            rmax = left_tile_rows(n, r, j1, qg, m, C)
+            rmax = left_tile_rows(n, r, j1, qg, m, C, TL)
             for T in range(nt):
-                c0 = right_tile_cols(n, r, j1, T)
+                c0 = right_tile_cols(n, r, j1, T, TL)
                 if c0 is None:
                     continue
                 rows = (T * TL + 1, min((T + 1) * TL, n))
@@ -171,13 +171,13 @@ def test_schedule_covers_and_orders(probe, n, r, q):
                 if r0 > r1 or c0 > c1:
                     continue
                 for T in range(nt):
-                    cf = right_tile_cols(n, r, j1, T)
+                    cf = right_tile_cols(n, r, j1, T, TL)
                     if cf is None:
                         continue
                     if T * TL + 1 <= r1 and min((T + 1) * TL, n) >= r0 and c1 >= cf:
                         assert P["T0"] <= T <= nr, ("step does not wait for right tile", j, k, m, T, nr)
                 for C in range(nt):
-                    rmax = left_tile_rows(n, r, j1, qg, m, C)
+                    rmax = left_tile_rows(n, r, j1, qg, m, C, TL)
                     if rmax is None:
                         continue
                     if C * TL + 1 <= c1 and min((C + 1) * TL, n) >= c0 and r0 <= rmax and r1 >= j1 + 1:
@@ -185,5 +185,5 @@ def test_schedule_covers_and_orders(probe, n, r, q):
 
 
 def test_closing_launch_has_only_qz_tiles(probe):
-    P, tasks, _ = run_probe(probe, 300, 16, 1, 16, ab=0, nqz=1)
+    P, tasks, _ = run_probe(probe, 300, 16, 1, 16, 32, ab=0, nqz=1)
     assert P["total"] == P["ntiles"] and all(k == 3 for _, k, _, _, _ in tasks)
