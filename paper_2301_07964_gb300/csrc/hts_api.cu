@@ -118,6 +118,7 @@ hts_status check_emu(hts_gemm_mode mode, int r, int q, const hts_params *p)
 {
     if (mode != HTS_GEMM_EMU_BF16) return HTS_OK;
     if (p && p->emu_slices != 0 && p->emu_slices != 8) return HTS_ERR_UNSUPPORTED;
+    if (p && p->tile_m != 0 && p->tile_m != 32 && p->tile_m != 128) return HTS_ERR_UNSUPPORTED;
     return emu_supported(r, q) ? HTS_OK : HTS_ERR_UNSUPPORTED;
 }
 
@@ -290,13 +291,27 @@ ApplyArgs apply_args(double *M0, int ld0, int kind0, double *M1, int ld1, int ki
 // update of the group (pj1, pqg, pset), persistent blocks on the SMs the next chase leaves free.
 cudaError_t launch_update(hts_ctx *ctx, bool emu, const UpdSched &us, double *A, int lda, double *B, int ldb,
                           double *const *qzM, const int *qzld, const int *qzkind, int n, int r, int j1, int qg,
-                          int set, int pj1, int pqg, int pset, int q, const S2Ptrs &P, cudaStream_t st)
+                          int set, int pj1, int pqg, int pset, int q, const S2Ptrs &P, const CUtensorMap *maps,
+                          cudaStream_t st)
 {
     if (us.P.total <= 0) return cudaSuccess;
-    const int workers = emu ? update_emu_workers() : update_fp64_workers();
+    const int workers = maps ? update_tc_workers() : emu ? update_emu_workers() : update_fp64_workers();
     int ctas = imax(1, ctx->num_sms - 2 * q);
     ctas = imin(ctas, (us.P.total + workers - 1) / workers);
     int *status = ctx->d_status;
+    if (maps) {
+        // tensor-core kernel: maps[2 s] / maps[2 s + 1] are the Z / Q planes of set s
+        UpdTcArgs ua;
+        ua.map_z = maps[2 * set];
+        ua.map_q = maps[2 * set + 1];
+        ua.map_qz_z = maps[2 * pset];
+        ua.map_qz_q = maps[2 * pset + 1];
+        ua.right = emu_args(A, lda, 0, B, ldb, 1, n, r, j1, qg, P, set, status);
+        ua.left = emu_args(A, lda, 4, B, ldb, 5, n, r, j1, qg, P, set, status);
+        ua.qz = emu_args(qzM[0], qzld[0], qzkind[0], qzM[1], qzld[1], qzkind[1], n, r, pj1, pqg, P, pset, status);
+        ua.s = us;
+        return launch_s2_update_tc(ua, ctas, st);
+    }
     if (emu) {
         UpdEmuArgs ua;
         ua.right = emu_args(A, lda, 0, B, ldb, 1, n, r, j1, qg, P, set, status);
@@ -325,7 +340,7 @@ cudaError_t launch_update(hts_ctx *ctx, bool emu, const UpdSched &us, double *A,
 // group's A / B updates follow its chase on the caller's stream and only the Q / Z update
 // overlaps the next chase (side stream).
 hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B, int ldb,
-                      double *Q, int ldq, double *Z, int ldz, int q, int flags, hts_gemm_mode mode,
+                      double *Q, int ldq, double *Z, int ldz, int q, int flags, int tile_m, hts_gemm_mode mode,
                       void *work, cudaStream_t st)
 {
     if (n <= 2 || r <= 1) return HTS_OK;
@@ -342,9 +357,17 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
     const int qzld[2] = {Z ? ldz : ldq, ldq};
     const int qzkind[2] = {Z ? 2 : 3, 3};
     cudaStream_t side = lookahead ? ctx->upd : ctx->side;
+    // the emulated look-ahead updates run on the tcgen05 kernel (128-line tiles) unless the
+    // mma.sync kernel (32-line tiles) is asked for or the tensor maps cannot be made
+    CUtensorMap maps[2 * kSets];
+    bool tc = emu && lookahead && tile_m != 32 && update_tc_supported(r, q);
+    for (int b = 0; tc && b < kSets; ++b)
+        tc = encode_plane_map(&maps[2 * b], P.PZ[b], L.kdim) == cudaSuccess &&
+             encode_plane_map(&maps[2 * b + 1], P.PQ[b], L.kdim) == cudaSuccess;
+    const int TL = tc ? update_tc_lines() : 32;
 
     int group = 0, prev_set = 0, prev_j1 = 0, prev_qg = 0;
-    TaskPlan prev_plan = task_plan(n, r, 1, 1, false, 0, 32);
+    TaskPlan prev_plan = task_plan(n, r, 1, 1, false, 0, TL);
     GroupCost prev_gc{};
     for (int j1 = 1; j1 <= n - 2; j1 += q, ++group) {
         const int qg = imin(q, n - 2 - j1 + 1);
@@ -378,7 +401,7 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         if (emu) {
             FormUArgs fa;
             fa.n = n; fa.r = r; fa.j1 = j1; fa.qg = qg; fa.R = P.R[set];
-            fa.planesQ = P.PQ[set]; fa.planesZ = P.PZ[set]; fa.status = status;
+            fa.planesQ = P.PQ[set]; fa.planesZ = P.PZ[set]; fa.status = status; fa.umma = tc ? 1 : 0;
             ProfScope ps(ctx, st);
             if ((e = launch_s2_form_u(fa, st)) != cudaSuccess) return HTS_ERR_CUDA;
             ps.done(HTS_K_FORM_U, gc.f_form, 0.0);
@@ -389,12 +412,12 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
             if (cudaStreamWaitEvent(side, ctx->ev_gen[set], 0) != cudaSuccess) return HTS_ERR_CUDA;
             const int nq = group >= 1 ? nqz : 0;
             UpdSched us;
-            us.P = task_plan(n, r, j1, qg, true, nq, 32);
+            us.P = task_plan(n, r, j1, qg, true, nq, TL);
             us.tflags = P.tfl; us.epoch = (unsigned long long)(group + 1); us.ticket = P.tick + group;
             us.status = status; us.group = group; us.n = n; us.r = r;
             ProfScope ps(ctx, side);
             if ((e = launch_update(ctx, emu, us, A, lda, B, ldb, qzM, qzld, qzkind, n, r, j1, qg, set, prev_j1, prev_qg,
-                                   prev_set, q, P, side)) != cudaSuccess)
+                                   prev_set, q, P, tc ? maps : nullptr, side)) != cudaSuccess)
                 return HTS_ERR_CUDA;
             ps.done(HTS_K_UPDATE, gc.f_right + gc.f_stair + gc.f_left + (nq ? prev_gc.f_qz : 0.0),
                     gc.b_right + gc.b_stair + gc.b_left + (nq ? prev_gc.b_qz : 0.0),
@@ -452,12 +475,12 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         if (qz) {
             // the closing launch: the last group's Q / Z update
             UpdSched us;
-            us.P = task_plan(n, r, 1, 1, false, nqz, 32);
+            us.P = task_plan(n, r, 1, 1, false, nqz, TL);
             us.tflags = P.tfl; us.epoch = (unsigned long long)(group + 1); us.ticket = P.tick + group;
             us.status = status; us.group = group; us.n = n; us.r = r;
             ProfScope ps(ctx, side);
             if ((e = launch_update(ctx, emu, us, A, lda, B, ldb, qzM, qzld, qzkind, n, r, prev_j1, prev_qg, prev_set,
-                                   prev_j1, prev_qg, prev_set, q, P, side)) != cudaSuccess)
+                                   prev_j1, prev_qg, prev_set, q, P, tc ? maps : nullptr, side)) != cudaSuccess)
                 return HTS_ERR_CUDA;
             ps.done(HTS_K_UPDATE, prev_gc.f_qz, prev_gc.b_qz, emu ? prev_gc.m_qz : 0.0);
             if (cudaEventRecord(ctx->ev_upd[group % kSets], side) != cudaSuccess) return HTS_ERR_CUDA;
@@ -591,7 +614,7 @@ hts_status hts_reduce_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, dou
         if (compz == HTS_COMP_INIT && (s = cuda_status(launch_set_identity(Z, ldz, n, st))) != HTS_OK) return s;
         ps.done(HTS_K_UTIL, 0.0, 0.0);
     }
-    return run_stage2(ctx, n, r, A, lda, B, ldb, Qp, ldq, Zp, ldz, q, flags, mode, work, st);
+    return run_stage2(ctx, n, r, A, lda, B, ldb, Qp, ldq, Zp, ldz, q, flags, p ? p->tile_m : 0, mode, work, st);
 }
 
 static hts_status check_stage1_args(hts_ctx *ctx, int n, int r, const hts_params *p, void *work, size_t work_bytes)
@@ -675,7 +698,8 @@ hts_status hts_reduce(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
             return HTS_ERR_CUDA;
         ps.done(HTS_K_STAGE1, 0.0, 0.0);
     }
-    return run_stage2(ctx, n, r, A, lda, B, ldb, Qp, ldq, Zp, ldz, q, p ? p->flags : 0, mode, work, st);
+    return run_stage2(ctx, n, r, A, lda, B, ldb, Qp, ldq, Zp, ldz, q, p ? p->flags : 0, p ? p->tile_m : 0, mode, work,
+                      st);
 }
 
 hts_status hts_workspace_size_batched(int count, const int *n, const int *r, const hts_params *p, size_t *bytes)

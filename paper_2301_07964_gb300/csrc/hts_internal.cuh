@@ -4,6 +4,8 @@
 // scheduling code; AT() converts to a column-major offset.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the encoder is resolved at run time; no link to the driver library)
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -246,6 +248,7 @@ struct FormUArgs {
     ReflectorSet R;
     uint2 *planesQ, *planesZ;
     const int *status;
+    int umma;   // plane layout: 0 = mma.sync B fragments (emu.cu), 1 = tcgen05 operand (emu_tc.cu)
 };
 
 // Emulated delayed updates (emu.cu).  kind 0 = A rows, 1 = B rows (the staircase blocks of
@@ -302,6 +305,18 @@ struct UpdFp64Args {
     int smem_doubles;   // shared memory of one worker
 };
 int update_fp64_smem_doubles(int r, int qg);
+// tcgen05 update launch (emu_tc.cu): A / B of the group with the tensor maps of its U planes,
+// Q / Z of the previous group with its own.
+struct UpdTcArgs {
+    CUtensorMap map_z, map_q, map_qz_z, map_qz_q;
+    EmuArgs right, left, qz;
+    UpdSched s;
+};
+cudaError_t launch_s2_update_tc(const UpdTcArgs &a, int ctas, cudaStream_t st);
+cudaError_t encode_plane_map(CUtensorMap *map, const void *planes, int kdim);
+int update_tc_workers();
+int update_tc_lines();
+bool update_tc_supported(int r, int qg);
 int update_fp64_workers();
 int update_emu_workers();
 cudaError_t launch_s2_update_fp64(const UpdFp64Args &a, int ctas, cudaStream_t st);

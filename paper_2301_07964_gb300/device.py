@@ -52,9 +52,9 @@ class Reducer:
 
     def stage2(self, A: torch.Tensor, B: torch.Tensor, r: int, Q=None, Z=None,
                compq=b.HTS_COMP_UPDATE, compz=b.HTS_COMP_UPDATE, q=0, flags=0,
-               mode=b.HTS_GEMM_FP64, stream=None, check=True) -> int:
+               mode=b.HTS_GEMM_FP64, stream=None, check=True, tile_m=0) -> int:
         n = A.shape[0]
-        params = b.hts_params(q=q, flags=flags)
+        params = b.hts_params(q=q, flags=flags, tile_m=tile_m)
         work = self.workspace(n, r, params)
         if Q is None:
             compq = b.HTS_COMP_NONE
@@ -66,9 +66,9 @@ class Reducer:
             raise b.HTSError(st, "hts_reduce_stage2")
         return st
 
-    def _call(self, fn, name, A, B, r, Q, Z, compq, compz, q, p, flags, mode, stream, check):
+    def _call(self, fn, name, A, B, r, Q, Z, compq, compz, q, p, flags, mode, stream, check, tile_m=0):
         n = A.shape[0]
-        params = b.hts_params(q=q, p=p, flags=flags)
+        params = b.hts_params(q=q, p=p, flags=flags, tile_m=tile_m)
         work = self.workspace(n, r, params)
         if Q is None:
             compq = b.HTS_COMP_NONE
@@ -86,8 +86,9 @@ class Reducer:
                           mode, stream, check)
 
     def reduce(self, A, B, r, Q=None, Z=None, compq=b.HTS_COMP_UPDATE, compz=b.HTS_COMP_UPDATE, q=0, p=0,
-               flags=0, mode=b.HTS_GEMM_FP64, stream=None, check=True) -> int:
-        return self._call(b.hts_reduce, "hts_reduce", A, B, r, Q, Z, compq, compz, q, p, flags, mode, stream, check)
+               flags=0, mode=b.HTS_GEMM_FP64, stream=None, check=True, tile_m=0) -> int:
+        return self._call(b.hts_reduce, "hts_reduce", A, B, r, Q, Z, compq, compz, q, p, flags, mode, stream, check,
+                          tile_m)
 
     def sync_status(self, stream=None):
         return b.hts_sync_status(self.ctx, stream)

@@ -171,3 +171,33 @@ def test_emu_full_size_properties(red, n, seed):
     for key in ("bwd_A", "bwd_B", "orth_Q", "orth_Z"):
         assert e[key] < 1e-12 * n, e
         assert e[key] <= 1.5 * f[key], (key, e, f)
+
+
+@pytest.mark.parametrize("n,q", [(40, 16), (129, 16), (300, 16), (513, 9), (700, 16)])
+def test_tensor_core_and_warp_kernels_match_oracle(red, oracle_mod, n, q):
+    """The emulated updates run either on the tcgen05 kernel (128-line tiles, TMEM accumulators,
+    U planes by TMA; the default) or on the mma.sync kernel (32-line tiles): both must give the
+    oracle's reduction within 1e-12 n, and agree with each other."""
+    from paper_2301_07964_gb300.device import colmajor_empty, to_device, to_host
+    r = 16
+    A, B = random_rht_pencil(n, r, 71 * n + q)
+    scale = max(1.0, float(np.abs(A).max()), float(np.abs(B).max()))
+    Ho, To, Qo, Zo = oracle_mod.stage2(A, B, r)
+    o = canonical(Ho, To, Qo, Zo)
+    res = []
+    for tile_m in (128, 32):
+        dA, dB = to_device(A), to_device(B)
+        dQ, dZ = colmajor_empty(n), colmajor_empty(n)
+        red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, mode=EMU, tile_m=tile_m)
+        st, info = red.sync_status()
+        assert st == b.HTS_OK, (tile_m, b.status_string(st), info)
+        H, T, Q, Z = (to_host(x) for x in (dA, dB, dQ, dZ))
+        c = rht_pencil_checks(A, B, H, T, Q, Z)
+        assert c["H_below_hessenberg"] == 0.0 and c["T_below_diag"] == 0.0, (tile_m, c)
+        for key in ("bwd_A", "bwd_B", "orth_Q", "orth_Z"):
+            assert c[key] < 1e-14 * max(n, 10), (tile_m, c)
+        g = canonical(H, T, Q, Z)
+        err = max(float(np.abs(x - y).max()) for x, y in zip(g, o)) / scale
+        assert err <= 1e-12 * n, (tile_m, err)
+        res.append(g)
+    assert max(float(np.abs(x - y).max()) for x, y in zip(*res)) / scale <= 1e-12 * n
