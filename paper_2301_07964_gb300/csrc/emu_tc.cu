@@ -139,17 +139,37 @@ __device__ __forceinline__ void tc_commit(unsigned long long *bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tc_ld8(unsigned taddr, unsigned (&v)[8])
+// The 8 levels of 8 consecutive positions (TMEM columns 32 L + c0 .. 32 L + c0 + 7 of the
+// warp's 32 lanes) in one statement together with the wait for them: tcgen05.ld writes its
+// registers asynchronously, so nothing may read (or move) them before tcgen05.wait::ld, and
+// keeping both in one asm statement leaves the compiler no room to do so.  The memory clobber
+// keeps the statement after the MMA-completion wait and the thread-sync fence before it.
+__device__ __forceinline__ void tc_ld_levels(unsigned taddr, unsigned (&v)[kDigits][8])
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                 : "r"(taddr));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%65];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%66];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%67];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32, %33, %34, %35, %36, %37, %38, %39}, [%68];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%40, %41, %42, %43, %44, %45, %46, %47}, [%69];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%48, %49, %50, %51, %52, %53, %54, %55}, [%70];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%56, %57, %58, %59, %60, %61, %62, %63}, [%71];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[0][2]), "=r"(v[0][3]), "=r"(v[0][4]), "=r"(v[0][5]), "=r"(v[0][6]),
+          "=r"(v[0][7]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[1][2]), "=r"(v[1][3]), "=r"(v[1][4]), "=r"(v[1][5]),
+          "=r"(v[1][6]), "=r"(v[1][7]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(v[2][2]), "=r"(v[2][3]), "=r"(v[2][4]),
+          "=r"(v[2][5]), "=r"(v[2][6]), "=r"(v[2][7]), "=r"(v[3][0]), "=r"(v[3][1]), "=r"(v[3][2]), "=r"(v[3][3]),
+          "=r"(v[3][4]), "=r"(v[3][5]), "=r"(v[3][6]), "=r"(v[3][7]), "=r"(v[4][0]), "=r"(v[4][1]), "=r"(v[4][2]),
+          "=r"(v[4][3]), "=r"(v[4][4]), "=r"(v[4][5]), "=r"(v[4][6]), "=r"(v[4][7]), "=r"(v[5][0]), "=r"(v[5][1]),
+          "=r"(v[5][2]), "=r"(v[5][3]), "=r"(v[5][4]), "=r"(v[5][5]), "=r"(v[5][6]), "=r"(v[5][7]), "=r"(v[6][0]),
+          "=r"(v[6][1]), "=r"(v[6][2]), "=r"(v[6][3]), "=r"(v[6][4]), "=r"(v[6][5]), "=r"(v[6][6]), "=r"(v[6][7]),
+          "=r"(v[7][0]), "=r"(v[7][1]), "=r"(v[7][2]), "=r"(v[7][3]), "=r"(v[7][4]), "=r"(v[7][5]), "=r"(v[7][6]),
+          "=r"(v[7][7])
+        : "r"(taddr), "r"(taddr + kWin), "r"(taddr + 2 * kWin), "r"(taddr + 3 * kWin), "r"(taddr + 4 * kWin),
+          "r"(taddr + 5 * kWin), "r"(taddr + 6 * kWin), "r"(taddr + 7 * kWin)
+        : "memory");
 }
-
-__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// Orders a register written by tcgen05.ld after the preceding tcgen05.wait::ld.
-__device__ __forceinline__ void reg_after_wait(unsigned &x) { asm volatile("" : "+r"(x)::"memory"); }
 
 // Byte offset of (row m, k) in a K-major core-matrix layout with K = 32.
 __device__ __forceinline__ unsigned kmaj_off(int m, int k)
@@ -232,6 +252,9 @@ __device__ void tc_tile(const TcTile &t, int tile, TcWorker &W, unsigned long lo
         double fresh[kWin];
         long long carry[16];
         int cu = 0;
+        bool bad = false;                 // this thread met a wait that ran out
+        int u_pend = buf;                 // buffer with a TMA copy in flight (thread 0), or -1
+        unsigned u_par = ph.u[buf];       // the phase that copy completes
 #pragma unroll
         for (int p = 0; p < kWin; ++p) fresh[p] = 0.0;
 #pragma unroll
@@ -282,14 +305,18 @@ __device__ void tc_tile(const TcTile &t, int tile, TcWorker &W, unsigned long lo
             }
             fence_async_smem();
             tc_fence_before();
-            group_sync(wb, kTcThreads);
-            if (*(volatile int *)abort) break;
+            if (group_sync_or(wb, kTcThreads, bad)) {
+                bad = true;
+                break;
+            }
             if (tid == 0) {
                 tc_fence_after();
                 if (!mbar_wait(&bar_u[buf], ph.u[buf])) {
                     record_error(status, HTS_ERR_TIMEOUT, 0, -2, k, tile);
-                    *(volatile int *)abort = 1;
+                    bad = true;
+                    tc_commit(bar_d);   // no MMAs: the others' wait ends, the tile stops next
                 } else {
+                    u_pend = -1;
                     const unsigned a0 = smem_u32(W.A), b0 = smem_u32(W.U[buf]);
 #pragma unroll
                     for (int i = 0; i < kDigits; ++i) {
@@ -305,6 +332,8 @@ __device__ void tc_tile(const TcTile &t, int tile, TcWorker &W, unsigned long lo
                     if (k - 1 >= K_lo) {
                         mbar_expect_tx(&bar_u[buf ^ 1], kUBytes);
                         tma_load_3d(W.U[buf ^ 1], t.map, 0, 0, k - 1, &bar_u[buf ^ 1]);
+                        u_pend = buf ^ 1;
+                        u_par = ph.u[buf ^ 1];
                     }
                 }
             }
@@ -323,7 +352,7 @@ __device__ void tc_tile(const TcTile &t, int tile, TcWorker &W, unsigned long lo
             }
             if (!mbar_wait(bar_d, ph.d)) {
                 record_error(status, HTS_ERR_TIMEOUT, 0, -3, k, tile);
-                *(volatile int *)abort = 1;
+                bad = true;
             }
             ph.d ^= 1u;
             tc_fence_after();
@@ -333,13 +362,7 @@ __device__ void tc_tile(const TcTile &t, int tile, TcWorker &W, unsigned long lo
 #pragma unroll
             for (int c = 0; c < kWin / 8; ++c) {
                 unsigned lv[kDigits][8];
-#pragma unroll
-                for (int L = 0; L < kDigits; ++L) tc_ld8(tl + kWin * L + 8 * c, lv[L]);
-                tc_wait_ld();
-#pragma unroll
-                for (int L = 0; L < kDigits; ++L)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) reg_after_wait(lv[L][j]);
+                tc_ld_levels(tl + 8 * c, lv);
                 if (act) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -360,7 +383,16 @@ __device__ void tc_tile(const TcTile &t, int tile, TcWorker &W, unsigned long lo
             if (act) cu = cu_new;
             tc_fence_before();
         }
-        group_sync(wb, kTcThreads);
+        if (group_sync_or(wb, kTcThreads, bad)) {
+            // stop the tile: let a copy into U that is still in flight land (bounded) before
+            // the buffer is reused or the block exits, and the other tiles of this worker end
+            if (tid == 0) {
+                if (u_pend >= 0 && !mbar_wait(&bar_u[u_pend], u_par)) record_error(status, HTS_ERR_TIMEOUT, 0, -4, 0, tile);
+                *(volatile int *)abort = 1;
+            }
+            group_sync(wb, kTcThreads);
+            return;
+        }
     }
 
     // staircase blocks of the right updates of A and B, per 32-row subtile, in native FP64
@@ -418,7 +450,8 @@ __global__ void __launch_bounds__(kTcThreads * kTcWorkers, 1) k_s2_update_tc(con
     ph.d = 0;
     const int wb = 1 + worker;
     update_worker<kTcThreads>(a.s, tid, wb, &S.slot[worker], [&](const Task &T) {
-        if (S.abort[worker]) return;
+        // an empty slot of the ticket layout (a row of the plan without this kind of tile)
+        if (S.abort[worker] || T.kind == kTaskNone) return;
         TcTile tt;
         if (T.kind == kTaskQZ) {
             tt.X = a.qz.M[T.mat]; tt.ld = (size_t)a.qz.ld[T.mat]; tt.kind = a.qz.kind[T.mat];

@@ -180,6 +180,19 @@ __device__ __forceinline__ void group_sync(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// The same barrier, returning whether any thread of the group passed v = true: a decision
+// (stop, skip) that every thread of the group takes alike.
+__device__ __forceinline__ bool group_sync_or(int id, int nthreads, bool v)
+{
+    int any;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(any)
+        : "r"(v ? 1 : 0), "r"(id), "r"(nthreads)
+        : "memory");
+    return any != 0;
+}
+
 // Brackets one kernel launch with profiler events when profiling is on (profile.cu).
 struct ProfScope {
     hts_ctx *ctx;
