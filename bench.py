@@ -313,7 +313,7 @@ def run_ours(args, n, r):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, mode=mode,
-                   flags=sched_flags, stream=stream)
+                   flags=sched_flags, stream=stream, tile_m=args.tile_m)
         e1.record(stream)
         return e0, e1
 
@@ -380,7 +380,7 @@ def run_ours(args, n, r):
             dA.t().copy_(hA, non_blocking=True)
             dB.t().copy_(hB, non_blocking=True)
             red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, mode=mode,
-                       flags=sched_flags, stream=stream)
+                       flags=sched_flags, stream=stream, tile_m=args.tile_m)
             for o, d in zip(outs, (dA, dB, dQ, dZ)):
                 o.copy_(d.t(), non_blocking=True)
             torch.cuda.synchronize()
@@ -437,6 +437,7 @@ def run_ours(args, n, r):
                                "a Gaussian), Q and Z accumulated, delayed updates %s" % (n, r, q, args.mode),
                    "n": n, "r": r, "q": q, "mode": args.mode, "parallelism": "replicas" if ws > 1 else "single",
                    "schedule": "serial" if args.serial else "look-ahead",
+                   "update_tiles": args.tile_m or "library default",
                    "l2": "inputs (A, B: %.1f GiB) larger than L2" % (2 * 8 * n * n / 2 ** 30)},
         "backward_error": bwd,
         "direct_gflops": ws * 8.0 * n ** 3 / (ms / 1e3) / 1e9,
@@ -540,7 +541,8 @@ def run_probe(args, n, r):
     for _ in range(2):
         dA, dB = to_device(A), to_device(B)
         dQ, dZ = colmajor_empty(n), colmajor_empty(n)
-        red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, mode=mode)
+        red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, mode=mode,
+                   tile_m=args.tile_m)
         st, info = red.sync_status()
         if st != b.HTS_OK:
             raise SystemExit("device error: %s %s" % (b.status_string(st), info))
@@ -619,6 +621,8 @@ def main():
     ap.add_argument("--q", type=int, default=0)
     ap.add_argument("--serial", action="store_true",
                     help="stage 2: each group's delayed updates after its chase (no look-ahead)")
+    ap.add_argument("--tile-m", type=int, default=0, choices=[0, 32, 128],
+                    help="emulated update tiles: 128 lines (tcgen05), 32 (mma.sync), 0 the library's choice")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
