@@ -198,10 +198,13 @@ hts_status hts_reduce(hts_ctx *ctx, int n, int r,
  * pencils of possibly different sizes in one launch.  The array arguments are host arrays
  * of length count (device pointers for the matrices); compq / compz apply to every pencil.
  * Each pencil is reduced by one thread block with its reflectors applied one at a time, so
- * the batch, not a single pencil, supplies the parallelism; blocks start largest pencil
- * first.  Limits of this path: n_i <= 512, r_i <= 16 and r_i < n_i (or n_i <= 2),
- * p * r_i <= 64 (p defaults to min(8, 64/r_i)).  `work` holds the pencil descriptors:
- * hts_workspace_size_batched() bytes.  The results equal those of hts_reduce up to rounding.
+ * the batch, not a single pencil, supplies the parallelism.  The launch is persistent: as many
+ * blocks as the SMs hold at once take pencils from a device queue, largest pencil first.
+ * Limits of this path: n_i <= 512, r_i <= 16 and r_i < n_i (or n_i <= 2),
+ * p * r_i <= 64 (p defaults to min(8, 64/r_i)).  `work` (256-byte aligned,
+ * hts_workspace_size_batched() bytes) holds the pencil descriptors, the order and the queue.
+ * The results equal those of hts_reduce up to rounding.  Equivalent to hts_plan_batched
+ * followed by hts_reduce_batched_planned.
  */
 hts_status hts_workspace_size_batched(int count, const int *n, const int *r, const hts_params *p,
                                       size_t *bytes);
@@ -211,6 +214,28 @@ hts_status hts_reduce_batched(hts_ctx *ctx, int count, const int *n, const int *
                               hts_comp compz, double *const *Z, const int *ldz,
                               hts_gemm_mode mode, const hts_params *p, void *work, size_t work_bytes,
                               void *stream);
+
+/*
+ * The batched reduction in two parts, for a batch that is reduced many times with the same
+ * matrix pointers (new values each time), and for CUDA graphs:
+ *  - hts_plan_batched checks the arguments as hts_reduce_batched does and writes the batch's
+ *    descriptors, largest-first order, compq / compz and p into `work` (an asynchronous copy
+ *    on `stream`; the host arrays may be released when it returns).  It reads no matrix.
+ *  - hts_reduce_batched_planned reduces the planned batch: it resets the queue counter in
+ *    `work` and launches the persistent kernel, both on `stream`, using no host data but
+ *    `count`.  It may be captured into a CUDA graph and replayed; the plan must stay in
+ *    `work`, and work must not be shared by launches that overlap on the GPU.
+ * Errors: HTS_ERR_ARG, HTS_ERR_UNSUPPORTED as for hts_reduce_batched; HTS_ERR_WORKSPACE when
+ * work is null, not 256-byte aligned or shorter than hts_workspace_size_batched(); HTS_ERR_CUDA.
+ * Device errors (HTS_ERR_NONFINITE with the pencil index) through hts_sync_status.
+ */
+hts_status hts_plan_batched(hts_ctx *ctx, int count, const int *n, const int *r,
+                            double *const *A, const int *lda, double *const *B, const int *ldb,
+                            hts_comp compq, double *const *Q, const int *ldq,
+                            hts_comp compz, double *const *Z, const int *ldz,
+                            hts_gemm_mode mode, const hts_params *p, void *work, size_t work_bytes,
+                            void *stream);
+hts_status hts_reduce_batched_planned(hts_ctx *ctx, int count, void *work, size_t work_bytes, void *stream);
 
 /*
  * Wait for `stream`, then report and clear the context's device status word.

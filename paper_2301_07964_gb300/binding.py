@@ -92,6 +92,11 @@ def load(path: str = LIB_PATH):
     lib.hts_reduce_batched.argtypes = [_VP, _I, IP, IP, PP, IP, PP, IP, _I, PP, IP, _I, PP, IP, _I,
                                        ctypes.POINTER(hts_params), _VP, ctypes.c_size_t, _VP]
     lib.hts_reduce_batched.restype = _I
+    lib.hts_plan_batched.argtypes = [_VP, _I, IP, IP, PP, IP, PP, IP, _I, PP, IP, _I, PP, IP, _I,
+                                     ctypes.POINTER(hts_params), _VP, ctypes.c_size_t, _VP]
+    lib.hts_plan_batched.restype = _I
+    lib.hts_reduce_batched_planned.argtypes = [_VP, _I, _VP, ctypes.c_size_t, _VP]
+    lib.hts_reduce_batched_planned.restype = _I
     lib.hts_sync_status.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int)]
     lib.hts_sync_status.restype = _I
     lib.hts_status_string.argtypes = [_I]
@@ -213,6 +218,22 @@ def hts_workspace_size_batched(n, r, params=None) -> int:
     if st != HTS_OK:
         raise HTSError(st, "hts_workspace_size_batched")
     return out.value
+
+
+def hts_plan_batched(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode, params, work, work_bytes,
+                     stream=None) -> int:
+    """Same arguments as hts_reduce_batched; writes the plan into work."""
+    count = len(n)
+    Qs = Q if Q is not None else [None] * count
+    Zs = Z if Z is not None else [None] * count
+    return load().hts_plan_batched(ctx, count, _iarr(n), _iarr(r), _parr(A), _iarr(lda), _parr(B), _iarr(ldb),
+                                   int(compq), _parr(Qs), _iarr(ldq if ldq is not None else [1] * count),
+                                   int(compz), _parr(Zs), _iarr(ldz if ldz is not None else [1] * count),
+                                   int(mode), _params(params), _ptr(work), int(work_bytes), _stream(stream))
+
+
+def hts_reduce_batched_planned(ctx, count, work, work_bytes, stream=None) -> int:
+    return load().hts_reduce_batched_planned(ctx, int(count), _ptr(work), int(work_bytes), _stream(stream))
 
 
 def hts_reduce_batched(ctx, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode, params, work, work_bytes,

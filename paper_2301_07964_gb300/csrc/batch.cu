@@ -6,6 +6,8 @@
 // column for left applications, one thread per row for right applications).  Blocks are
 // launched largest pencil first, so the hardware's in-order block dispatch gives a
 // longest-processing-time schedule; many small pencils keep every SM busy.
+#include <algorithm>
+
 #include "hts_internal.cuh"
 
 namespace hts {
@@ -199,11 +201,17 @@ struct BatchDesc {
     int n, r, lda, ldb, ldq, ldz;
 };
 
-__global__ void __launch_bounds__(kBT) k_reduce_batched(const BatchDesc *desc, const int *order, int p_param,
-                                                         int compq, int compz, int *status)
+__host__ __device__ __forceinline__ size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+// What a launch reads besides the descriptors: written once by the plan, then fixed.
+struct BatchHead {
+    int count, compq, compz, p;
+};
+
+// Reduction of pencil pid (its descriptor d) by the whole block.
+__device__ void reduce_pencil(const BatchDesc &d, int pid, int p_param, int compq, int compz, int *status,
+                              BatchShared &S)
 {
-    __shared__ BatchShared S;
-    const BatchDesc d = desc[order[blockIdx.x]];
     const int n = d.n, r = d.r;
     double *A = d.A, *B = d.B;
     double *Q = compq ? d.Q : nullptr, *Z = compz ? d.Z : nullptr;
@@ -221,7 +229,7 @@ __global__ void __launch_bounds__(kBT) k_reduce_batched(const BatchDesc *desc, c
                                  ((__double_as_longlong(Z[AT(d.ldz, i, c)]) >> 52) & 0x7ff) == 0x7ff) ? 4
                                                                                                   : 0;
             if (which) {
-                record_error(status, HTS_ERR_NONFINITE, order[blockIdx.x], which - 1, i, c);
+                record_error(status, HTS_ERR_NONFINITE, pid, which - 1, i, c);
                 bad = 1;
             }
         }
@@ -323,21 +331,72 @@ __global__ void __launch_bounds__(kBT) k_reduce_batched(const BatchDesc *desc, c
     }
 }
 
-cudaError_t launch_reduce_batched(const void *desc, const int *order, int count, int p, int compq, int compz,
-                                  int *status, cudaStream_t st)
+// Persistent launch: each block takes the next pencil of the largest-first order from a device
+// queue (one atomic counter, zeroed before the launch) until the batch is used up.  The queue
+// keeps the longest-processing-time order of a one-block-per-pencil launch while the grid stays
+// at what the SMs hold at once.
+__global__ void __launch_bounds__(kBT) k_reduce_batched(const BatchHead *head, unsigned *next, const BatchDesc *desc,
+                                                         const int *order, int *status)
 {
-    k_reduce_batched<<<count, kBT, 0, st>>>(static_cast<const BatchDesc *>(desc), order, p, compq, compz, status);
-    return cudaGetLastError();
+    __shared__ BatchShared S;
+    __shared__ int s_idx;
+    const BatchHead h = *head;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = (int)atomicAdd(next, 1u);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();   // s_idx is taken again by the next round
+        if (idx >= h.count) return;
+        const int pid = order[idx];
+        reduce_pencil(desc[pid], pid, h.p, h.compq, h.compz, status, S);
+        __syncthreads();
+    }
 }
 
-size_t batch_desc_bytes() { return sizeof(BatchDesc); }
-
-void fill_batch_desc(void *dst, int i, double *A, double *B, double *Q, double *Z, int n, int r, int lda, int ldb,
-                     int ldq, int ldz)
+// Workspace of a batch: [head | queue counter at byte 128] [descriptors] [order], each part
+// 256-byte aligned.
+size_t batch_work_bytes(int count)
 {
-    BatchDesc *d = static_cast<BatchDesc *>(dst) + i;
-    d->A = A; d->B = B; d->Q = Q; d->Z = Z;
-    d->n = n; d->r = r; d->lda = lda; d->ldb = ldb; d->ldq = ldq; d->ldz = ldz;
+    return 256 + round256((size_t)count * sizeof(BatchDesc)) + round256((size_t)count * sizeof(int));
+}
+
+void batch_stage(void *host, int count, const int *n, const int *r, double *const *A, const int *lda,
+                 double *const *B, const int *ldb, double *const *Q, const int *ldq, double *const *Z, const int *ldz,
+                 int compq, int compz, int p)
+{
+    unsigned char *w = static_cast<unsigned char *>(host);
+    BatchHead *h = reinterpret_cast<BatchHead *>(w);
+    h->count = count; h->compq = compq; h->compz = compz; h->p = p;
+    *reinterpret_cast<unsigned *>(w + 128) = 0u;
+    BatchDesc *d = reinterpret_cast<BatchDesc *>(w + 256);
+    int *order = reinterpret_cast<int *>(w + 256 + round256((size_t)count * sizeof(BatchDesc)));
+    for (int i = 0; i < count; ++i) {
+        d[i].A = A[i]; d[i].B = B[i];
+        d[i].Q = compq ? Q[i] : nullptr; d[i].Z = compz ? Z[i] : nullptr;
+        d[i].n = n[i]; d[i].r = r[i]; d[i].lda = lda[i]; d[i].ldb = ldb[i];
+        d[i].ldq = compq ? ldq[i] : 1; d[i].ldz = compz ? ldz[i] : 1;
+        order[i] = i;
+    }
+    std::stable_sort(order, order + count, [&](int a, int b2) { return n[a] > n[b2]; });
+}
+
+cudaError_t launch_reduce_batched(void *work, int count, int num_sms, int *status, cudaStream_t st)
+{
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_reduce_batched, kBT, 0) != cudaSuccess || b < 1) b = 1;
+        per_sm = b;
+    }
+    unsigned char *w = static_cast<unsigned char *>(work);
+    cudaError_t e = cudaMemsetAsync(w + 128, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    const int grid = imax(1, imin(count, per_sm * num_sms));
+    const size_t off_order = 256 + round256((size_t)count * sizeof(BatchDesc));
+    k_reduce_batched<<<grid, kBT, 0, st>>>(reinterpret_cast<const BatchHead *>(w), reinterpret_cast<unsigned *>(w + 128),
+                                           reinterpret_cast<const BatchDesc *>(w + 256),
+                                           reinterpret_cast<const int *>(w + off_order), status);
+    return cudaGetLastError();
 }
 
 int batch_max_n() { return kBatchMaxN; }

@@ -708,7 +708,75 @@ hts_status hts_workspace_size_batched(int count, const int *n, const int *r, con
     if (!bytes || count < 0 || (count > 0 && (!n || !r))) return HTS_ERR_ARG;
     for (int i = 0; i < count; ++i)
         if (n[i] < 0 || r[i] < 1) return HTS_ERR_ARG;
-    *bytes = align_up((size_t)count * batch_desc_bytes(), 256) + align_up((size_t)count * sizeof(int), 256) + 256;
+    *bytes = batch_work_bytes(count) + 256;
+    return HTS_OK;
+}
+
+namespace {
+
+// Argument checks shared by the batched calls; *pp receives stage 1's p (0: the default).
+hts_status check_batched(int count, const int *n, const int *r, double *const *A, const int *lda, double *const *B,
+                         const int *ldb, hts_comp compq, double *const *Q, const int *ldq, hts_comp compz,
+                         double *const *Z, const int *ldz, hts_gemm_mode mode, const hts_params *p, int *pp)
+{
+    if (!n || !r || !A || !lda || !B || !ldb) return HTS_ERR_ARG;
+    if (compq < HTS_COMP_NONE || compq > HTS_COMP_UPDATE || compz < HTS_COMP_NONE || compz > HTS_COMP_UPDATE)
+        return HTS_ERR_ARG;
+    if ((compq != HTS_COMP_NONE && (!Q || !ldq)) || (compz != HTS_COMP_NONE && (!Z || !ldz))) return HTS_ERR_ARG;
+    if (mode != HTS_GEMM_FP64 && mode != HTS_GEMM_EMU_BF16) return HTS_ERR_ARG;
+    if (mode != HTS_GEMM_FP64) return HTS_ERR_UNSUPPORTED;
+    *pp = (p && p->p > 0) ? p->p : 0;
+    for (int i = 0; i < count; ++i) {
+        if (n[i] < 1 || r[i] < 1 || (n[i] > 2 && r[i] >= n[i])) return HTS_ERR_ARG;
+        if (bad_matrix(A[i], lda[i], n[i]) || bad_matrix(B[i], ldb[i], n[i])) return HTS_ERR_ARG;
+        if (compq != HTS_COMP_NONE && bad_matrix(Q[i], ldq[i], n[i])) return HTS_ERR_ARG;
+        if (compz != HTS_COMP_NONE && bad_matrix(Z[i], ldz[i], n[i])) return HTS_ERR_ARG;
+        if (n[i] > batch_max_n() || r[i] > 16) return HTS_ERR_UNSUPPORTED;
+        const int pe = *pp > 0 ? *pp : imin(8, imax(2, batch_max_block() / r[i]));
+        if (pe < 2 || pe * r[i] > batch_max_block()) return HTS_ERR_UNSUPPORTED;
+    }
+    return HTS_OK;
+}
+
+bool batch_work_ok(const void *work, size_t work_bytes, int count)
+{
+    return work && !(reinterpret_cast<uintptr_t>(work) & 255u) && work_bytes >= batch_work_bytes(count);
+}
+
+}  // namespace
+
+hts_status hts_plan_batched(hts_ctx *ctx, int count, const int *n, const int *r, double *const *A, const int *lda,
+                            double *const *B, const int *ldb, hts_comp compq, double *const *Q, const int *ldq,
+                            hts_comp compz, double *const *Z, const int *ldz, hts_gemm_mode mode,
+                            const hts_params *p, void *work, size_t work_bytes, void *stream)
+{
+    if (!ctx || count < 1) return HTS_ERR_ARG;
+    int pp = 0;
+    const hts_status cs = check_batched(count, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode, p, &pp);
+    if (cs != HTS_OK) return cs;
+    if (!batch_work_ok(work, work_bytes, count)) return HTS_ERR_WORKSPACE;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return HTS_ERR_CUDA;
+    // the workspace image (descriptors and the largest-first order) staged on the host; a copy
+    // from pageable memory is staged by the runtime before cudaMemcpyAsync returns
+    std::vector<unsigned char> img(batch_work_bytes(count));
+    batch_stage(img.data(), count, n, r, A, lda, B, ldb, Q, ldq, Z, ldz, (int)compq, (int)compz, pp);
+    if (cudaMemcpyAsync(work, img.data(), img.size(), cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream)) !=
+        cudaSuccess)
+        return HTS_ERR_CUDA;
+    return HTS_OK;
+}
+
+hts_status hts_reduce_batched_planned(hts_ctx *ctx, int count, void *work, size_t work_bytes, void *stream)
+{
+    if (!ctx || count < 1) return HTS_ERR_ARG;
+    if (!batch_work_ok(work, work_bytes, count)) return HTS_ERR_WORKSPACE;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return HTS_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ProfScope ps(ctx, st);
+    if (launch_reduce_batched(work, count, ctx->num_sms, ctx->d_status, st) != cudaSuccess) return HTS_ERR_CUDA;
+    ps.done(HTS_K_BATCH, 0.0, 0.0);
     return HTS_OK;
 }
 
@@ -721,51 +789,10 @@ hts_status hts_reduce_batched(hts_ctx *ctx, int count, const int *n, const int *
 {
     if (!ctx || count < 0) return HTS_ERR_ARG;
     if (count == 0) return HTS_OK;
-    if (!n || !r || !A || !lda || !B || !ldb) return HTS_ERR_ARG;
-    if (compq < HTS_COMP_NONE || compq > HTS_COMP_UPDATE || compz < HTS_COMP_NONE || compz > HTS_COMP_UPDATE)
-        return HTS_ERR_ARG;
-    if ((compq != HTS_COMP_NONE && (!Q || !ldq)) || (compz != HTS_COMP_NONE && (!Z || !ldz))) return HTS_ERR_ARG;
-    if (mode != HTS_GEMM_FP64 && mode != HTS_GEMM_EMU_BF16) return HTS_ERR_ARG;
-    if (mode != HTS_GEMM_FP64) return HTS_ERR_UNSUPPORTED;
-    const int pp = (p && p->p > 0) ? p->p : 0;
-    for (int i = 0; i < count; ++i) {
-        if (n[i] < 1 || r[i] < 1 || (n[i] > 2 && r[i] >= n[i])) return HTS_ERR_ARG;
-        if (bad_matrix(A[i], lda[i], n[i]) || bad_matrix(B[i], ldb[i], n[i])) return HTS_ERR_ARG;
-        if (compq != HTS_COMP_NONE && bad_matrix(Q[i], ldq[i], n[i])) return HTS_ERR_ARG;
-        if (compz != HTS_COMP_NONE && bad_matrix(Z[i], ldz[i], n[i])) return HTS_ERR_ARG;
-        if (n[i] > batch_max_n() || r[i] > 16) return HTS_ERR_UNSUPPORTED;
-        const int pe = pp > 0 ? pp : imin(8, imax(2, batch_max_block() / r[i]));
-        if (pe < 2 || pe * r[i] > batch_max_block()) return HTS_ERR_UNSUPPORTED;
-    }
-    size_t need = 0;
-    hts_workspace_size_batched(count, n, r, p, &need);
-    if (!work || (reinterpret_cast<uintptr_t>(work) & 255u) || work_bytes < need) return HTS_ERR_WORKSPACE;
-    DeviceGuard g(ctx->device);
-    if (!g.ok) return HTS_ERR_CUDA;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // descriptors and the largest-first order, staged on the host
-    const size_t dbytes = align_up((size_t)count * batch_desc_bytes(), 256);
-    std::vector<unsigned char> hdesc((size_t)count * batch_desc_bytes());
-    std::vector<int> order(count);
-    for (int i = 0; i < count; ++i) {
-        fill_batch_desc(hdesc.data(), i, A[i], B[i], compq ? Q[i] : nullptr, compz ? Z[i] : nullptr, n[i], r[i],
-                        lda[i], ldb[i], compq ? ldq[i] : 1, compz ? ldz[i] : 1);
-        order[i] = i;
-    }
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b2) { return n[a] > n[b2]; });
-    char *w = static_cast<char *>(work);
-    if (cudaMemcpyAsync(w, hdesc.data(), hdesc.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(w + dbytes, order.data(), sizeof(int) * (size_t)count, cudaMemcpyHostToDevice, st) !=
-            cudaSuccess)
-        return HTS_ERR_CUDA;
-    ProfScope ps(ctx, st);
-    if (launch_reduce_batched(w, reinterpret_cast<const int *>(w + dbytes), count, pp, (int)compq, (int)compz,
-                              ctx->d_status, st) != cudaSuccess)
-        return HTS_ERR_CUDA;
-    ps.done(HTS_K_BATCH, 0.0, 0.0);
-    // the host staging vectors may go now: copies from pageable memory are staged by the
-    // runtime before cudaMemcpyAsync returns
-    return HTS_OK;
+    const hts_status s = hts_plan_batched(ctx, count, n, r, A, lda, B, ldb, compq, Q, ldq, compz, Z, ldz, mode, p,
+                                          work, work_bytes, stream);
+    if (s != HTS_OK) return s;
+    return hts_reduce_batched_planned(ctx, count, work, work_bytes, stream);
 }
 
 hts_status hts_fallback_count(hts_ctx *ctx, void *stream, long long *count)

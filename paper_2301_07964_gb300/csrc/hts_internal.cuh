@@ -338,13 +338,13 @@ cudaError_t launch_set_identity(double *M, int ld, int n, cudaStream_t st);
 cudaError_t launch_zero_below(double *M, int ld, int n, int band, const int *status, cudaStream_t st);
 cudaError_t launch_scan_nonfinite(const double *M, int ld, int n, int lower, int which, int *status, cudaStream_t st);
 
-// Batched reduction (batch.cu).
-struct BatchDesc;
-cudaError_t launch_reduce_batched(const void *desc, const int *order, int count, int p, int compq, int compz,
-                                  int *status, cudaStream_t st);
-size_t batch_desc_bytes();
-void fill_batch_desc(void *dst, int i, double *A, double *B, double *Q, double *Z, int n, int r, int lda, int ldb,
-                     int ldq, int ldz);
+// Batched reduction (batch.cu): the workspace holds a head, the queue counter, the
+// descriptors and the largest-first order; batch_stage writes that image in host memory.
+size_t batch_work_bytes(int count);
+void batch_stage(void *host, int count, const int *n, const int *r, double *const *A, const int *lda,
+                 double *const *B, const int *ldb, double *const *Q, const int *ldq, double *const *Z, const int *ldz,
+                 int compq, int compz, int p);
+cudaError_t launch_reduce_batched(void *work, int count, int num_sms, int *status, cudaStream_t st);
 int batch_max_n();
 int batch_max_block();
 

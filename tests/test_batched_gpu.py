@@ -116,3 +116,66 @@ def test_batch_config_4096_pencils(red, oracle_mod):
         scale = max(np.abs(A).max(), np.abs(B).max())
         err = max(float(np.abs(x - y).max()) for x, y in zip(gg, oo)) / scale
         assert err <= 1e-12 * n, (i, n, err)
+
+
+def test_planned_launches_and_cuda_graph_match_one_call(red):
+    """hts_plan_batched once, then hts_reduce_batched_planned twice on fresh copies of the
+    inputs, and the planned launch captured in a CUDA graph and replayed twice: every result
+    equals the single hts_reduce_batched call's bit for bit (the same kernel on the same
+    pencil, whichever block of the persistent launch takes it)."""
+    from paper_2301_07964_gb300.device import colmajor_empty, to_device, to_host
+    sizes = [5, 40, 64, 100, 130, 200, 33, 17, 3, 96]
+    rs = [max(1, min(8, n // 8)) if n > 2 else 1 for n in sizes]
+    pencils = [random_pencil(n, 700 + i) for i, n in enumerate(sizes)]
+    ref = [[to_host(x) for x in mats] for mats in zip(*_run_batch(red, pencils, rs))]
+    A0 = [to_device(A) for A, _ in pencils]
+    B0 = [to_device(B) for _, B in pencils]
+    dA, dB, dQ, dZ = ([colmajor_empty(n) for n in sizes] for _ in range(4))
+    nbytes = b.hts_workspace_size_batched(sizes, rs)
+    work = torch.empty(max(256, nbytes), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    st = b.hts_plan_batched(red.ctx, sizes, rs, dA, sizes, dB, sizes, b.HTS_COMP_INIT, dQ, sizes, b.HTS_COMP_INIT,
+                            dZ, sizes, b.HTS_GEMM_FP64, None, work, work.numel(), stream)
+    assert st == b.HTS_OK, b.status_string(st)
+
+    def restore():
+        for x, y in zip(dA + dB, A0 + B0):
+            x.copy_(y)
+        for x in dQ + dZ:
+            x.fill_(float("nan"))   # COMP_INIT overwrites them
+
+    def check(what):
+        torch.cuda.synchronize()
+        dst, info = red.sync_status()
+        assert dst == b.HTS_OK, (what, info)
+        for i in range(len(sizes)):
+            got = [to_host(x) for x in (dA[i], dB[i], dQ[i], dZ[i])]
+            for g, e, name in zip(got, ref[i], "HTQZ"):
+                assert np.array_equal(g, e), (what, sizes[i], name, float(np.nanmax(np.abs(g - e))))
+
+    for rep in range(2):
+        restore()
+        st = b.hts_reduce_batched_planned(red.ctx, len(sizes), work, work.numel(), stream)
+        assert st == b.HTS_OK, b.status_string(st)
+        check("planned launch %d" % rep)
+
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph):
+        st = b.hts_reduce_batched_planned(red.ctx, len(sizes), work, work.numel(), torch.cuda.current_stream())
+    assert st == b.HTS_OK, b.status_string(st)
+    for rep in range(2):
+        restore()
+        torch.cuda.synchronize()
+        graph.replay()
+        check("graph replay %d" % rep)
+
+
+def test_planned_launch_rejects_bad_workspace(red):
+    n, r = [40, 50], [4, 4]
+    need = b.hts_workspace_size_batched(n, r)
+    work = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+    assert b.hts_reduce_batched_planned(red.ctx, 2, None, need) == b.HTS_ERR_WORKSPACE
+    assert b.hts_reduce_batched_planned(red.ctx, 2, work.data_ptr() + 8, need) == b.HTS_ERR_WORKSPACE
+    assert b.hts_reduce_batched_planned(red.ctx, 2, work, 64) == b.HTS_ERR_WORKSPACE
+    assert b.hts_reduce_batched_planned(red.ctx, 0, work, need) == b.HTS_ERR_ARG
