@@ -56,7 +56,7 @@ def test_sweep_work_sums_to_the_direct_count():
 
 
 def test_traffic_is_reported_only_for_the_captured_source(tmp_path, monkeypatch):
-    digest = bench.source_digest("chase16.cu")
+    digest = bench.source_digest(bench.KERNEL_SOURCES["k_s2_chase16"])
     rec = tmp_path / "ncu_traffic.txt"
     rec.write_text("# kernel workload bytes digest\n"
                    "k_s2_chase16 wl_a 12345 %s\n"
