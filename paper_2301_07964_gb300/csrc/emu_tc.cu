@@ -34,8 +34,10 @@
 // stores its whole window after its last block; inactive lines contribute no loads and no
 // stores (their rows of A_i are left as they are and their results are discarded).
 //
-// One block per SM (512 threads at up to 128 registers), 256 TMEM columns; thread 0 issues
-// the MMAs and the TMA copies, the next window's U_k is copied while the current one is used.
+// One block per SM (512 threads at up to 128 registers), all 512 TMEM columns as two
+// accumulators of 256, so that the MMAs of window k run while the half of window k+1 that
+// leaves the window is combined and stored; thread 0 issues the MMAs and the TMA copies, the
+// next window's U_k is copied while the current one is used.
 // The blocks take tiles from the look-ahead schedule (schedule.cuh).
 #include <cuda.h>
 
@@ -76,7 +78,7 @@ struct TcShared {
     unsigned char U[2][kUBytes];              // U_k and U_{k-1} (2 x 16 KiB)
     int em[kTcSplit][kTcLines];               // exponents of the threads' parts of the window
     unsigned long long bar_u[2];              // TMA of U into buffer b
-    unsigned long long bar_d;                 // the window's MMAs are done
+    unsigned long long bar_d[2];              // the MMAs into accumulator b are done
     unsigned tmem_base;
     int slot;
     int abort;
@@ -189,7 +191,7 @@ __device__ __forceinline__ unsigned kmaj_off(int m, int k)
 // Pipeline state of the block (the same in every thread).
 struct TcPhase {
     unsigned u[2];   // parity of the next phase of bar_u[b]
-    unsigned d;      // parity of the next phase of bar_d
+    unsigned d[2];   // parity of the next phase of bar_d[b]
 };
 
 // Arguments of one tile: the matrix, its kind (0, 1 right A / B; 2, 3 Z / Q; 4, 5 left A / B),
@@ -219,6 +221,31 @@ __device__ __forceinline__ void load_part(const TcTile &t, int line, int h, int 
     for (int j = 0; j < kTcPos; ++j) {
         const int p = pos_of(h, j);
         v[j] = (j < jn && p < cnt && c0 + p <= t.n) ? *elem(t, line, c0 + p) : 0.0;
+    }
+}
+
+// One half of a window's results (half 0: positions 4h .. 4h+3, half 1: 16+4h .. 16+4h+3): the
+// 8 levels read from the accumulator at taddr (the thread's lane quarter, column 0 of the
+// accumulator), combined into integers in units 2^cu_new.  Positions that leave the window
+// (p >= w - r, or every position in the line's last window) are stored; half 0 keeps the
+// overlap (p < w - r) in carry.  The TMEM read is warp-wide, so every thread takes part.
+__device__ __forceinline__ void epilogue_half(const TcTile &t, int line, int h, unsigned taddr, int half, bool act,
+                                              bool last, int c0, int cu_new, int w, int r, long long (&carry)[4])
+{
+    unsigned lv[kDigits][4];
+    tc_ld_levels4(taddr + (unsigned)pos_of(h, 4 * half), lv);
+    if (!act) return;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+        const int p = pos_of(h, 4 * half + jj);
+        if (p < w) {
+            const long long v = combine_levels(__uint_as_float(lv[0][jj]), __uint_as_float(lv[1][jj]),
+                                               __uint_as_float(lv[2][jj]), __uint_as_float(lv[3][jj]),
+                                               __uint_as_float(lv[4][jj]), __uint_as_float(lv[5][jj]),
+                                               __uint_as_float(lv[6][jj]), __uint_as_float(lv[7][jj]));
+            if ((last || p >= w - r) && c0 + p <= t.n) *elem(t, line, c0 + p) = fixed_to_f64(v, cu_new);
+            if (half == 0) carry[jj] = (p < w - r) ? v : 0;
+        }
     }
 }
 
@@ -264,8 +291,13 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
     if (!lvalid) { khi = -1; klo = 0; }
 
     if (K_hi >= K_lo && K_hi >= 0) {
+        // Software pipeline over the windows, two TMEM accumulators (columns 0 and 256):
+        //   window k:   exponent, digits and MMAs (they need the overlap of window k+1),
+        //   meanwhile   the positions of window k+1 that leave it (second half) are combined and stored,
+        //   then        window k's first half (the overlap of window k-1) is combined.
+        // The chain from one window to the next is thus first half, exponent, digits, MMA.
         const unsigned tl = tmem + ((unsigned)(32 * qd) << 16);
-        int buf = 0;
+        int ubuf = 0, dbuf = 0;
         int u_pend = 0;               // thread 0: buffer with a TMA copy in flight, or -1
         unsigned u_par = ph.u[0];     // the phase that copy completes
         bool bad = false;             // this thread met a wait that ran out
@@ -280,13 +312,17 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
             load_part(t, line, h, j1 + K_hi * r + 1, K_hi == khi ? w : r, K_hi == khi ? kTcPos : 4, fresh);
         else
             load_part(t, line, h, 0, 0, 0, fresh);
+        // the window whose second half is still in TMEM
+        bool p_act = false;
+        int p_c0 = 0, p_cu = 0;
 
-        for (int k = K_hi; k >= K_lo; --k) {
+        int k = K_hi;
+        for (;; --k) {
             const bool act = k <= khi && k >= klo;
             const bool first = k == khi;
             const bool last = k == klo;
             const int c0 = j1 + k * r + 1;
-            // the window's unit: 2^(ua + 62) above its largest entry, over the line's 4 threads
+            // ---- window k: the unit 2^(ua + 62) above its largest entry, over the line's 4 threads
             int e = kZeroExp;
             if (act) {
 #pragma unroll
@@ -328,68 +364,64 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
             }
             if (tid == 0) {
                 tc_fence_after();
-                if (!mbar_wait(&S.bar_u[buf], ph.u[buf])) {
+                if (!mbar_wait(&S.bar_u[ubuf], ph.u[ubuf])) {
                     record_error(status, HTS_ERR_TIMEOUT, 0, -2, k, tile);
                     bad = true;
-                    tc_commit(&S.bar_d);   // no MMAs: the others' wait ends, the tile stops next
+                    tc_commit(&S.bar_d[dbuf]);   // no MMAs: the others' wait ends, the tile stops next
                 } else {
                     u_pend = -1;
-                    const unsigned a0 = smem_u32(S.A), b0 = smem_u32(S.U[buf]);
+                    const unsigned a0 = smem_u32(S.A), b0 = smem_u32(S.U[ubuf]);
+                    const unsigned dcol = tmem + (unsigned)(dbuf * kTmemCols);
 #pragma unroll
                     for (int i = 0; i < kDigits; ++i) {
                         const unsigned idesc = kIdescBase | ((unsigned)((kWin * (kDigits - i)) >> 3) << 17);
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk)
-                            tc_mma(tmem + kWin * i, smem_desc(a0 + i * kDigitPlane + kk * 2 * kLBO),
+                            tc_mma(dcol + kWin * i, smem_desc(a0 + i * kDigitPlane + kk * 2 * kLBO),
                                    smem_desc(b0 + kk * 2 * kLBO), idesc, (i > 0 || kk > 0) ? 1 : 0);
                     }
-                    tc_commit(&S.bar_d);
+                    tc_commit(&S.bar_d[dbuf]);
                     // U of the next block into the other buffer (its last reader, the previous
                     // window's MMAs, has completed)
                     if (k - 1 >= K_lo) {
-                        mbar_expect_tx(&S.bar_u[buf ^ 1], kUBytes);
-                        tma_load_3d(S.U[buf ^ 1], t.map, 0, 0, k - 1, &S.bar_u[buf ^ 1]);
-                        u_pend = buf ^ 1;
-                        u_par = ph.u[buf ^ 1];
+                        mbar_expect_tx(&S.bar_u[ubuf ^ 1], kUBytes);
+                        tma_load_3d(S.U[ubuf ^ 1], t.map, 0, 0, k - 1, &S.bar_u[ubuf ^ 1]);
+                        u_pend = ubuf ^ 1;
+                        u_par = ph.u[ubuf ^ 1];
                     }
                 }
             }
-            ph.u[buf] ^= 1u;
-            buf ^= 1;
+            ph.u[ubuf] ^= 1u;
+            ubuf ^= 1;
             // the next window's new positions, while the MMAs run (this window's are consumed)
             {
                 const int kn = k - 1;
                 if (kn >= K_lo && kn <= khi && kn >= klo)
                     load_part(t, line, h, j1 + kn * r + 1, kn == khi ? w : r, kn == khi ? kTcPos : 4, fresh);
             }
-            if (!mbar_wait(&S.bar_d, ph.d)) {
+            // ---- the second half of window k+1 (positions 16 .. w-1 leave it), while the MMAs run
+            if (k < K_hi) epilogue_half(t, line, h, tl + (unsigned)((dbuf ^ 1) * kTmemCols), 1, p_act, true, p_c0, p_cu,
+                                        w, r, carry);
+            // ---- the first half of window k: the overlap of window k-1 (and position 15)
+            if (!mbar_wait(&S.bar_d[dbuf], ph.d[dbuf])) {
                 record_error(status, HTS_ERR_TIMEOUT, 0, -3, k, tile);
                 bad = true;
             }
-            ph.d ^= 1u;
+            ph.d[dbuf] ^= 1u;
             tc_fence_after();
-            // levels -> results; positions that leave the window are stored, the overlap is kept
-            const int cu_new = ua + 3;
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                unsigned lv[kDigits][4];
-                tc_ld_levels4(tl + pos_of(h, 4 * half), lv);
-                if (act) {
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        const int p = pos_of(h, 4 * half + jj);
-                        if (p < w) {
-                            const long long v = combine_levels(
-                                __uint_as_float(lv[0][jj]), __uint_as_float(lv[1][jj]), __uint_as_float(lv[2][jj]),
-                                __uint_as_float(lv[3][jj]), __uint_as_float(lv[4][jj]), __uint_as_float(lv[5][jj]),
-                                __uint_as_float(lv[6][jj]), __uint_as_float(lv[7][jj]));
-                            if ((last || p >= w - r) && c0 + p <= n) *elem(t, line, c0 + p) = fixed_to_f64(v, cu_new);
-                            if (half == 0) carry[jj] = (p < w - r) ? v : 0;
-                        }
-                    }
-                }
-            }
-            if (act) cu = cu_new;
+            epilogue_half(t, line, h, tl + (unsigned)(dbuf * kTmemCols), 0, act, last, c0, ua + 3, w, r, carry);
+            p_act = act;
+            p_c0 = c0;
+            p_cu = ua + 3;
+            if (act) cu = ua + 3;
+            dbuf ^= 1;
+            tc_fence_before();
+            if (k == K_lo) break;
+        }
+        // the second half of the last window
+        if (!bad) {
+            tc_fence_after();
+            epilogue_half(t, line, h, tl + (unsigned)((dbuf ^ 1) * kTmemCols), 1, p_act, true, p_c0, p_cu, w, r, carry);
             tc_fence_before();
         }
         if (group_sync_or(kWorkerBar, kTcThreads, bad)) {
@@ -438,14 +470,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_s2_update_tc(const __grid_con
     const int tid = threadIdx.x;
     if (tid < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
-                     "r"(kTmemCols)
+                     "r"(2 * kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
         mbar_init(&S.bar_u[0], 1);
         mbar_init(&S.bar_u[1], 1);
-        mbar_init(&S.bar_d, 1);
+        mbar_init(&S.bar_d[0], 1);
+        mbar_init(&S.bar_d[1], 1);
         S.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -455,7 +488,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_s2_update_tc(const __grid_con
     const unsigned tmem = S.tmem_base;
     TcPhase ph;
     ph.u[0] = ph.u[1] = 0;
-    ph.d = 0;
+    ph.d[0] = ph.d[1] = 0;
     update_worker<kTcThreads>(a.s, tid, kWorkerBar, &S.slot, [&](const Task &T) {
         // an empty slot of the ticket layout (a row of the plan without this kind of tile)
         if (*(volatile int *)&S.abort || T.kind == kTaskNone) return;
@@ -476,7 +509,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_s2_update_tc(const __grid_con
     __syncthreads();
     tc_fence_after();
     if (tid < 32)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(kTmemCols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(2 * kTmemCols)
                      : "memory");
 }
 
