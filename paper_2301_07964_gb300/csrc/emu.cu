@@ -95,20 +95,20 @@ __global__ void __launch_bounds__(128) k_s2_form_u(FormUArgs a)
     }
     __syncwarp();
     if (a.umma) {
-        // tcgen05 B operand of block k: the transposed digit planes U_t^T stacked along N
+        // tcgen05 B operand of block k: the transposed FP16 digit planes U_t^T stacked along N
         // (N = 32 t + output position, K = input position), K-major core matrices of 8 x 16
         // bytes, LBO 128 B, SBO 512 B.  Lane = input position; lanes 2i, 2i+1 share a word.
         unsigned char *blk = reinterpret_cast<unsigned char *>((fam ? a.planesZ : a.planesQ) + (size_t)k * kPlaneWords);
         for (int col = 0; col < 32; ++col) {
             unsigned d[kDigits];
-            digits_bf16(f64_to_fixed(U[lane * 33 + col], kUnitU), d);
+            digit_pairs_f16(f64_to_fixed(U[lane * 33 + col], kUnitU), 0, d);   // low halves
 #pragma unroll
             for (int t = 0; t < kDigits; ++t) {
                 const unsigned nb = __shfl_down_sync(0xffffffffu, d[t], 1);
                 if ((lane & 1) == 0) {
                     const int nn = 32 * t + col;
                     const size_t off = (size_t)(nn >> 3) * 512 + (lane >> 3) * 128 + (nn & 7) * 16 + (lane & 7) * 2;
-                    *reinterpret_cast<unsigned *>(blk + off) = pack_bf16(d[t], nb);
+                    *reinterpret_cast<unsigned *>(blk + off) = pack_f16(d[t], nb);
                 }
             }
         }

@@ -125,5 +125,51 @@ __device__ __forceinline__ long long combine_levels(float c2f, float c3f, float 
     return (hi << 32) + ((long long)mid << 16) + (long long)lo;
 }
 
+// ---- FP16 digit pairs (the tcgen05 kernel's operands) --------------------------------------
+
+// FP16 bit patterns of the 8 balanced base-256 digits of two values x0, x1 (|x| < 2^62), most
+// significant first, packed in pairs: word i holds digit i of x0 in its low half and of x1 in
+// its high half.  With u = x + 0x8080808080808080, digit i is byte 7-i of u minus 128.  One byte
+// permute places the two bytes under the FP16 exponent of 2^10 (the halves read 1024 + byte,
+// exactly, since FP16 steps by 1 in [1024, 2048)), one AND/OR clears the other bytes and sets
+// that exponent, and one packed FP16 subtraction of 1024 + 128 leaves the digits, exact because
+// they are integers of magnitude at most 128.
+__device__ __forceinline__ void digit_pairs_f16(long long x0, long long x1, unsigned (&w)[kDigits])
+{
+    const unsigned long long u0 = (unsigned long long)x0 + 0x8080808080808080ULL;
+    const unsigned long long u1 = (unsigned long long)x1 + 0x8080808080808080ULL;
+    const unsigned h0 = (unsigned)(u0 >> 32), l0 = (unsigned)u0, h1 = (unsigned)(u1 >> 32), l1 = (unsigned)u1;
+#pragma unroll
+    for (int i = 0; i < kDigits; ++i) {
+        const unsigned by = 3u - (unsigned)(i & 3);   // byte of the word holding digit i
+        const unsigned sel = by | (by << 4) | ((by + 4u) << 8) | ((by + 4u) << 12);
+        const unsigned t = (__byte_perm(i < 4 ? h0 : l0, i < 4 ? h1 : l1, sel) & 0x00FF00FFu) | 0x64006400u;
+        unsigned d;
+        asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(t), "r"(0x64806480u));
+        w[i] = d;
+    }
+}
+
+// Two FP16 values (the low halves of the words lo and hi) in one register, lo in the low half.
+__device__ __forceinline__ unsigned pack_f16(unsigned lo, unsigned hi) { return __byte_perm(lo, hi, 0x5410u); }
+
+// combine_levels with the FP32-to-integer bias of the levels removed once per group of levels
+// instead of once per level: bits(c + 1.5 2^23) = 0x4B400000 + c for the exact integers c, and
+// the sums below are taken modulo 2^32 (lo, mid) or 2^64 (hi), where the biases cancel exactly.
+__device__ __forceinline__ long long combine_levels_folded(float c2f, float c3f, float c4f, float c5f, float c6f,
+                                                           float c7f, float c8f, float c9f)
+{
+    constexpr unsigned K = 0x4B400000u;
+    const float m = 12582912.0f;
+    const unsigned b2 = __float_as_uint(c2f + m), b3 = __float_as_uint(c3f + m), b4 = __float_as_uint(c4f + m);
+    const unsigned b5 = __float_as_uint(c5f + m), b6 = __float_as_uint(c6f + m), b7 = __float_as_uint(c7f + m);
+    const unsigned b8 = __float_as_uint(c8f + m), b9 = __float_as_uint(c9f + m);
+    const int lo = (int)((b7 << 8) + b8 - K * 257u) + ((int)(b9 - (K - 128u)) >> 8);
+    const int mid = (int)((b5 << 8) + b6 - K * 257u);
+    const long long hi = (long long)(((unsigned long long)b2 << 16) + ((unsigned long long)b3 << 8) + b4 -
+                                     (unsigned long long)K * 65793ull);
+    return (hi << 32) + ((long long)mid << 16) + (long long)lo;
+}
+
 }  // namespace emu
 }  // namespace hts

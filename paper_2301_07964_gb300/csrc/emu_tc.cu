@@ -8,9 +8,10 @@
 // in emulated FP64 (emu_arith.cuh): every line is a fixed-point integer with its own
 // power-of-two unit, split into 8 base-256 digits, and the 36 digit pairs (i, t) with
 // i + t <= 7 are accumulated per level L = i + t in FP32 (exact: every partial sum is an
-// integer below 2^22).  With the 8 digit planes of the lines (A_i, 128 x 32 BF16) and U's 8
-// transposed digit planes stacked along N (B, 32 x 256 BF16), one MMA per digit i covers all
-// its levels at once:
+// integer below 2^22).  With the 8 digit planes of the lines (A_i, 128 x 32 FP16) and U's 8
+// transposed digit planes stacked along N (B, 32 x 256 FP16; a digit in [-128, 127] is exact in
+// FP16, and two of them come out of one byte permute and one packed subtraction), one MMA per
+// digit i covers all its levels at once:
 //     D[:, 32 i .. 255] += A_i B[:, 0 .. 255 - 32 i]      (M = 128, N = 32 (8 - i), K = 32),
 // so a window is 16 tcgen05.mma (two K = 16 steps per digit) into 256 TMEM columns, level L
 // at columns 32 L .. 32 L + 31.  The epilogue reads the levels back with tcgen05.ld, combines
@@ -64,9 +65,9 @@ constexpr int kStairGroup = 128;                    // threads per 32-row subtil
 constexpr int kStairDoubles = 2048;                 // shared scratch per subtile (16 KiB)
 constexpr unsigned kLBO = 128;                      // K-adjacent core matrices
 constexpr unsigned kSBO = 512;                      // row-group-adjacent core matrices
-// instruction descriptor of kind::f16: D FP32 (bit 4), A and B BF16 (bits 7, 10), both
-// K-major, M / 16 at bit 24; N / 8 goes to bit 17
-constexpr unsigned kIdescBase = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kTcLines >> 4) << 24);
+// instruction descriptor of kind::f16: D FP32 (bit 4), A and B FP16 (type 0 at bits 7 and 10),
+// both K-major, M / 16 at bit 24; N / 8 goes to bit 17
+constexpr unsigned kIdescBase = (1u << 4) | ((unsigned)(kTcLines >> 4) << 24);
 constexpr int kWorkerBar = 5;                       // the tile's barrier (1..4: staircase subtiles)
 
 static_assert(kTcSplit * kTcPos == kWin, "a line's positions are split over its threads");
@@ -239,7 +240,7 @@ __device__ __forceinline__ void epilogue_half(const TcTile &t, int line, int h, 
     for (int jj = 0; jj < 4; ++jj) {
         const int p = pos_of(h, 4 * half + jj);
         if (p < w) {
-            const long long v = combine_levels(__uint_as_float(lv[0][jj]), __uint_as_float(lv[1][jj]),
+            const long long v = combine_levels_folded(__uint_as_float(lv[0][jj]), __uint_as_float(lv[1][jj]),
                                                __uint_as_float(lv[2][jj]), __uint_as_float(lv[3][jj]),
                                                __uint_as_float(lv[4][jj]), __uint_as_float(lv[5][jj]),
                                                __uint_as_float(lv[6][jj]), __uint_as_float(lv[7][jj]));
@@ -341,19 +342,20 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
                 // this thread's digits, 4 positions (8 bytes per plane) at a time
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
-                    unsigned dg[4][kDigits];
+                    long long x[4];
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj) {
                         const int j = 4 * half + jj;
-                        long long x = 0;
-                        if (pos_of(h, j) < w) x = (first || j < 4) ? f64_to_fixed(fresh[j], ua) : refix(carry[jj], cu, ua);
-                        digits_bf16(x, dg[jj]);
+                        x[jj] = 0;
+                        if (pos_of(h, j) < w) x[jj] = (first || j < 4) ? f64_to_fixed(fresh[j], ua) : refix(carry[jj], cu, ua);
                     }
+                    unsigned d01[kDigits], d23[kDigits];
+                    digit_pairs_f16(x[0], x[1], d01);
+                    digit_pairs_f16(x[2], x[3], d23);
                     const unsigned off = kmaj_off(m, pos_of(h, 4 * half));
 #pragma unroll
                     for (int i = 0; i < kDigits; ++i)
-                        *reinterpret_cast<uint2 *>(S.A + i * kDigitPlane + off) =
-                            make_uint2(pack_bf16(dg[0][i], dg[1][i]), pack_bf16(dg[2][i], dg[3][i]));
+                        *reinterpret_cast<uint2 *>(S.A + i * kDigitPlane + off) = make_uint2(d01[i], d23[i]);
                 }
             }
             fence_async_smem();
