@@ -555,7 +555,7 @@ def run_reduce(args, n, r):
     def step():
         dA.copy_(dA0)
         dB.copy_(dB0)
-        red.reduce(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=args.q, stream=stream,
+        red.reduce(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=args.q, p=args.p, stream=stream,
                    mode=b.HTS_GEMM_FP64 if args.mode == "fp64" else b.HTS_GEMM_EMU_BF16)
 
     for _ in range(args.warmup):
@@ -584,7 +584,7 @@ def run_reduce(args, n, r):
         bwd["T_diag_zeros_at_least"] = n // 8
         bwd["T_diag_below_1e-12n"] = int((dT < 1e-12 * n).sum())
     kind = " ill-conditioned B" if args.ill else (" saddle point (n/4 infinite eigenvalues)" if args.saddle else "")
-    print(json.dumps({"workload": "full reduction n=%d r=%d%s, delayed updates %s" % (n, r, kind, args.mode),
+    print(json.dumps({"workload": "full reduction n=%d r=%d%s, delayed updates %s" % (n, r, kind, args.mode), "p": args.p,
                       "ms_per_step": ms, "stage01_ms": s01, "stage2_ms": ms - s01,
                       "gflops_two_stage_21.33n3": 21.33 * n ** 3 / (ms / 1e3) / 1e9,
                       "gflops_stage2_10n3": paper_flops(n) / ((ms - s01) / 1e3) / 1e9,
@@ -721,6 +721,7 @@ def main():
     ap.add_argument("--workload", choices=["stage2", "reduce", "batch", "probe"], default="stage2")
     ap.add_argument("--ill", action="store_true", help="reduce: ill-conditioned B")
     ap.add_argument("--saddle", action="store_true", help="reduce: saddle-point pencil")
+    ap.add_argument("--p", type=int, default=0, help="reduce: stage 1's blocks per panel step (0: the default)")
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--count", type=int, default=4096)
     args = ap.parse_args()

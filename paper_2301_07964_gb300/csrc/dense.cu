@@ -1,86 +1,13 @@
-// Dense FP64 building blocks of stages 0 and 1 (QR of B, Alg. 1): a tiled GEMM, Householder
-// QR of a panel, the triangular factor of a block reflector (forward, columnwise), and the
-// RQ + LQ factorisation of one B block that yields the opposite reflectors of Alg. 1.
+// Dense FP64 building blocks of stages 0 and 1 (QR of B, Alg. 1): Householder QR of a panel,
+// the triangular factor of a block reflector (forward, columnwise), and the RQ + LQ
+// factorisation of one B block that yields the opposite reflectors of Alg. 1.  The block
+// reflectors' products with the matrices are plain GEMMs, done by cuBLAS (stage01.cu).
 //
 // Block reflectors are used in compact WY form: H_1 H_2 ... H_b = I - V T V^T with V unit
 // lower trapezoidal (explicit ones and zeros) and T upper triangular (both dense buffers).
 #include "hts_internal.cuh"
 
 namespace hts {
-
-// ---------------------------------------------------------------------------------------
-// C = alpha op(A) op(B) + beta C, column-major, op(A) M x K, op(B) K x N.  beta = 0 does not
-// read C.  64 x 64 tiles, 256 threads, 4 x 4 outputs per thread, FP64 FMA.
-// ---------------------------------------------------------------------------------------
-constexpr int kGM = 64, kGN = 64, kGK = 16;
-
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha, const double *A, int lda,
-                                               const double *B, int ldb, double beta, double *C, int ldc)
-{
-    __shared__ double As[kGK][kGM + 1];
-    __shared__ double Bs[kGK][kGN + 1];
-    const int tid = threadIdx.x;
-    const int m0 = blockIdx.x * kGM, n0 = blockIdx.y * kGN;
-    const int tm = (tid % 16) * 4, tn = (tid / 16) * 4;
-    double acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += kGK) {
-        for (int e = tid; e < kGM * kGK; e += 256) {
-            int mm, kk;
-            if (!TA) { mm = e % kGM; kk = e / kGM; }
-            else { kk = e % kGK; mm = e / kGK; }
-            const int gm = m0 + mm, gk = k0 + kk;
-            double v = 0.0;
-            if (gm < M && gk < K) v = TA ? A[(size_t)gk + (size_t)gm * lda] : A[(size_t)gm + (size_t)gk * lda];
-            As[kk][mm] = v;
-        }
-        for (int e = tid; e < kGN * kGK; e += 256) {
-            int nn, kk;
-            if (!TB) { kk = e % kGK; nn = e / kGK; }
-            else { nn = e % kGN; kk = e / kGN; }
-            const int gn = n0 + nn, gk = k0 + kk;
-            double v = 0.0;
-            if (gn < N && gk < K) v = TB ? B[(size_t)gn + (size_t)gk * ldb] : B[(size_t)gk + (size_t)gn * ldb];
-            Bs[kk][nn] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kGK; ++kk) {
-            double a[4], bb[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][tm + i];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) bb[i] = Bs[kk][tn + i];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(a[i], bb[jj], acc[i][jj]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-            const int gm = m0 + tm + i, gn = n0 + tn + jj;
-            if (gm < M && gn < N) {
-                double *c = C + (size_t)gm + (size_t)gn * ldc;
-                *c = (beta == 0.0) ? alpha * acc[i][jj] : alpha * acc[i][jj] + beta * (*c);
-            }
-        }
-}
-
-cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda,
-                  const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t st)
-{
-    if (M <= 0 || N <= 0) return cudaSuccess;
-    dim3 grid((M + kGM - 1) / kGM, (N + kGN - 1) / kGN);
-    if (!ta && !tb) k_dgemm<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    else if (ta && !tb) k_dgemm<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    else if (!ta && tb) k_dgemm<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    else k_dgemm<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------------------
 // Householder QR of the m x b panel P (column-major, ld) in one thread block (dlarfg

@@ -537,7 +537,8 @@ hts_status hts_create(hts_ctx **ctx, int device)
               cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
               cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) == cudaSuccess &&
               cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, lo_prio) == cudaSuccess &&
-              cudaStreamCreateWithPriority(&c->upd, cudaStreamNonBlocking, lo_prio) == cudaSuccess;
+              cudaStreamCreateWithPriority(&c->upd, cudaStreamNonBlocking, lo_prio) == cudaSuccess &&
+              cublasCreate(&c->blas) == CUBLAS_STATUS_SUCCESS;
     for (int b = 0; ok && b < 3; ++b)
         ok = cudaEventCreateWithFlags(&c->ev_gen[b], cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&c->ev_qz[b], cudaEventDisableTiming) == cudaSuccess &&
@@ -565,6 +566,7 @@ void hts_destroy(hts_ctx *ctx)
         if (ctx->ev_qz[b]) cudaEventDestroy(ctx->ev_qz[b]);
         if (ctx->ev_upd[b]) cudaEventDestroy(ctx->ev_upd[b]);
     }
+    if (ctx->blas) cublasDestroy(ctx->blas);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->upd) cudaStreamDestroy(ctx->upd);
     if (ctx->d_status) cudaFree(ctx->d_status);
@@ -650,7 +652,7 @@ hts_status hts_reduce_stage1(hts_ctx *ctx, int n, int r, double *A, int lda, dou
     if (compq == HTS_COMP_INIT && launch_set_identity(Q, ldq, n, st) != cudaSuccess) return HTS_ERR_CUDA;
     if (compz == HTS_COMP_INIT && launch_set_identity(Z, ldz, n, st) != cudaSuccess) return HTS_ERR_CUDA;
     if (launch_zero_below(B, ldb, n, 0, ctx->d_status, st) != cudaSuccess) return HTS_ERR_CUDA;
-    if (run_stage1(n, r, stage1_p(p, r), A, lda, B, ldb, Qp, ldq, Zp, ldz, work, st) != cudaSuccess)
+    if (run_stage1(ctx->blas, n, r, stage1_p(p, r), A, lda, B, ldb, Qp, ldq, Zp, ldz, work, st) != cudaSuccess)
         return HTS_ERR_CUDA;
     ps.done(HTS_K_STAGE1, 0.0, 0.0);
     return HTS_OK;
@@ -673,7 +675,7 @@ hts_status hts_reduce(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         if ((s = scan_inputs(ctx, n, A, lda, n, B, ldb, n, compq, Q, ldq, compz, Z, ldz, st)) != HTS_OK) return s;
         if (compq == HTS_COMP_INIT && launch_set_identity(Q, ldq, n, st) != cudaSuccess) return HTS_ERR_CUDA;
         if (compz == HTS_COMP_INIT && launch_set_identity(Z, ldz, n, st) != cudaSuccess) return HTS_ERR_CUDA;
-        if (run_stage0(n, A, lda, B, ldb, compq == HTS_COMP_NONE ? nullptr : Q, ldq, work, r, stage1_p(p, r),
+        if (run_stage0(ctx->blas, n, A, lda, B, ldb, compq == HTS_COMP_NONE ? nullptr : Q, ldq, work, r, stage1_p(p, r),
                        st) != cudaSuccess)
             return HTS_ERR_CUDA;
         return HTS_OK;
@@ -693,8 +695,8 @@ hts_status hts_reduce(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
         if ((s = scan_inputs(ctx, n, A, lda, n, B, ldb, n, compq, Q, ldq, compz, Z, ldz, st)) != HTS_OK) return s;
         if (compq == HTS_COMP_INIT && launch_set_identity(Q, ldq, n, st) != cudaSuccess) return HTS_ERR_CUDA;
         if (compz == HTS_COMP_INIT && launch_set_identity(Z, ldz, n, st) != cudaSuccess) return HTS_ERR_CUDA;
-        if (run_stage0(n, A, lda, B, ldb, Qp, ldq, work, r, stage1_p(p, r), st) != cudaSuccess) return HTS_ERR_CUDA;
-        if (run_stage1(n, r, stage1_p(p, r), A, lda, B, ldb, Qp, ldq, Zp, ldz, work, st) != cudaSuccess)
+        if (run_stage0(ctx->blas, n, A, lda, B, ldb, Qp, ldq, work, r, stage1_p(p, r), st) != cudaSuccess) return HTS_ERR_CUDA;
+        if (run_stage1(ctx->blas, n, r, stage1_p(p, r), A, lda, B, ldb, Qp, ldq, Zp, ldz, work, st) != cudaSuccess)
             return HTS_ERR_CUDA;
         ps.done(HTS_K_STAGE1, 0.0, 0.0);
     }

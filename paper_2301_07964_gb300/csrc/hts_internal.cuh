@@ -4,6 +4,7 @@
 // scheduling code; AT() converts to a column-major offset.
 #pragma once
 
+#include <cublas_v2.h>
 #include <cuda.h>   // CUtensorMap (the encoder is resolved at run time; no link to the driver library)
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -34,6 +35,7 @@ struct hts_ctx {
     cudaEvent_t ev_qz[3];    // serial schedule: set s no longer read by its Q / Z update
     cudaEvent_t ev_upd[3];   // look-ahead: update launch u (u mod 3) finished
     int num_sms;
+    cublasHandle_t blas;     // the WY products of stages 0 and 1 (plain DGEMMs)
 };
 
 namespace hts {
@@ -352,9 +354,9 @@ int batch_max_block();
 size_t stage01_workspace_bytes(int n, int r, int p);
 size_t stage2_workspace_bytes(int n, int r);
 size_t stage2_workspace_bytes_mode(int n, int r, hts_gemm_mode mode);
-cudaError_t run_stage0(int n, double *A, int lda, double *B, int ldb, double *Q, int ldq, void *work, int r, int p,
+cudaError_t run_stage0(cublasHandle_t blas, int n, double *A, int lda, double *B, int ldb, double *Q, int ldq, void *work, int r, int p,
                        cudaStream_t st);
-cudaError_t run_stage1(int n, int nb, int p, double *A, int lda, double *B, int ldb, double *Q, int ldq,
+cudaError_t run_stage1(cublasHandle_t blas, int n, int nb, int p, double *A, int lda, double *B, int ldb, double *Q, int ldq,
                        double *Z, int ldz, void *work, cudaStream_t st);
 
 // Same reflector as warp_larfg with one reciprocal square root and one reciprocal on the
