@@ -113,7 +113,8 @@ void hts_destroy(hts_ctx *ctx);
 /* Bytes of `work` needed by hts_reduce_stage1 / hts_reduce_stage2 / hts_reduce for an n x n
  * pencil with r subdiagonals and parameters p (NULL = defaults).  The size covers all three
  * entry points and both update modes (HTS_GEMM_EMU_BF16 adds 64 KiB per block of r columns
- * for the digit planes of the reflector products). */
+ * for the digit planes of the reflector products; stages 0 and 1 include 4 MiB that the
+ * context's cuBLAS handle uses as its workspace for the block-reflector products). */
 hts_status hts_workspace_size(int n, int r, const hts_params *p, size_t *bytes);
 
 /*

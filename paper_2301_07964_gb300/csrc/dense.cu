@@ -116,19 +116,27 @@ __global__ void k_larft(int b, const double *S, int lds, const double *tau, doub
 
 // ---------------------------------------------------------------------------------------
 // Opposite reflectors of one filled B block (Alg. 1, right-hand part): RQ of the m x m block
-// W = R~ Q~ (Householder, last row first, reflectors kept in the zeroed part of W), then the
-// LQ factorisation of the first l rows of Q~; the LQ reflectors (unit upper... stored as
-// columns of V, m x l, unit lower trapezoidal in the block's column index) and tau_lq are
-// returned.  Applying H_1 ... H_l from the right reduces the first l columns of the block.
-// One thread block; W and the l x m matrix M = Q~(0:l, :) live in shared memory.
+// W = R~ Q~ (Householder, last row first), then the LQ factorisation of the first l rows of Q~;
+// the LQ reflectors (stored as columns of V, m x l, unit lower trapezoidal in the block's column
+// index) and tau_lq are returned.  Applying H_1 ... H_l from the right reduces the first l
+// columns of the block.  One thread block; W and the l x m matrix M = Q~(0:l, :) live in
+// shared memory.
+//
+// The RQ is bound by the SM's FP64 throughput (2 FMA per clock), so its reflectors are kept
+// as u = x - beta e_s with tau = 1 / (beta (beta - alpha)) (no rescaling pass, one
+// reciprocal), the scalars of a step are formed by warp 0 alone, and the rows are updated four
+// lanes to a row, all rows in one pass: the dot products then need two shuffle-adds per eight
+// rows instead of a five-level warp reduction per row.  The row stride m + 4 keeps the four
+// lanes of the eight rows of a warp on distinct banks.
 // ---------------------------------------------------------------------------------------
 constexpr int kRQThreads = 512;
+constexpr int kRQPad = 4;
 
 __global__ void __launch_bounds__(kRQThreads) k_block_rq_lq(int m, int l, const double *Bblk, int ldb,
                                                              double *V, int ldv, double *tau_lq)
 {
     extern __shared__ double sh[];
-    const int ldw = m + 1;
+    const int ldw = m + kRQPad;
     double *W = sh;                          // m x m, row-major: W[i * ldw + c]
     double *Ms = W + (size_t)m * ldw;        // l x m, row-major
     double *rqt = Ms + (size_t)l * ldw;      // m taus of the RQ reflectors
@@ -143,42 +151,53 @@ __global__ void __launch_bounds__(kRQThreads) k_block_rq_lq(int m, int l, const 
         W[i * ldw + c] = Bblk[(size_t)i + (size_t)c * ldb];
     }
     __syncthreads();
-    // RQ: for s = m-1 .. 1 (0-based pivot row s, pivot column s)
+    // RQ: for s = m-1 .. 1 (0-based pivot row s, pivot column s); reflector u_s in row s of W
+    // (u_s(s) = alpha - beta), tau in rqt[s] (0: the identity)
+    const int row = tid >> 2, sub = tid & 3;   // m <= 128 = kRQThreads / 4 rows: one pass
     for (int s = m - 1; s >= 1; --s) {
-        double part = 0.0;
-        for (int c = tid; c < s; c += kRQThreads) part += W[s * ldw + c] * W[s * ldw + c];
-        const double ssq = block_sum(part, red);
-        if (tid == 0) {
-            const double alpha = W[s * ldw + s];
-            if (ssq == 0.0) {
-                s_tau = 0.0; s_beta = alpha; s_scale = 0.0;
-            } else {
-                const double nrm = sqrt(alpha * alpha + ssq);
-                const double beta = (alpha >= 0.0) ? -nrm : nrm;
-                s_tau = (beta - alpha) / beta;
-                s_scale = 1.0 / (alpha - beta);
-                s_beta = beta;
+        if (warp == 0) {
+            double p0 = 0.0, p1 = 0.0;
+            for (int c = lane; c < s; c += 64) {
+                p0 = fma(W[s * ldw + c], W[s * ldw + c], p0);
+                if (c + 32 < s) p1 = fma(W[s * ldw + c + 32], W[s * ldw + c + 32], p1);
             }
-            rqt[s] = s_tau;
-        }
-        __syncthreads();
-        const double ts = s_tau;
-        // reflector vector (v_s = 1, v_c = W(s, c) * scale for c < s) kept in row s
-        for (int c = tid; c < s; c += kRQThreads) W[s * ldw + c] *= s_scale;
-        __syncthreads();
-        if (ts != 0.0) {
-            for (int row = warp; row < s; row += nw) {
-                double d = 0.0;
-                for (int c = lane; c <= s; c += 32) d += W[row * ldw + c] * (c == s ? 1.0 : W[s * ldw + c]);
-                d = warp_sum(d) * ts;
-                for (int c = lane; c <= s; c += 32) W[row * ldw + c] -= d * (c == s ? 1.0 : W[s * ldw + c]);
+            const double ssq = warp_sum(p0 + p1);
+            if (lane == 0) {
+                const double alpha = W[s * ldw + s];
+                double tau = 0.0;
+                if (ssq != 0.0) {
+                    const double nrm = sqrt(fma(alpha, alpha, ssq));
+                    const double beta = (alpha >= 0.0) ? -nrm : nrm;
+                    tau = 1.0 / (beta * (beta - alpha));
+                    W[s * ldw + s] = alpha - beta;
+                }
+                rqt[s] = tau;
             }
         }
-        if (tid == 0) W[s * ldw + s] = s_beta;
+        __syncthreads();
+        const double ts = rqt[s];
+        // rows 0 .. s-1 := row - tau (row . u) u^T; a warp whose rows are all >= s skips
+        if (ts != 0.0 && (warp << 3) < s) {
+            const bool act = row < s;
+            const double *u = W + (size_t)s * ldw;
+            double *w = W + (size_t)row * ldw;
+            double d0 = 0.0, d1 = 0.0;
+            if (act)
+                for (int c = sub; c <= s; c += 8) {
+                    d0 = fma(w[c], u[c], d0);
+                    if (c + 4 <= s) d1 = fma(w[c + 4], u[c + 4], d1);
+                }
+            double d = d0 + d1;
+            d += __shfl_xor_sync(0xffffffffu, d, 1);
+            d += __shfl_xor_sync(0xffffffffu, d, 2);
+            d *= ts;
+            if (act)
+                for (int c = sub; c <= s; c += 4) w[c] = fma(-d, u[c], w[c]);
+        }
         __syncthreads();
     }
-    // M = E_l^T H_1' H_2' ... with the RQ reflectors in the order that forms Q~ = G^T:
-    // Q~ = H_(1) H_(2) ... H_(m-1) where H_(s) acts on columns 0..s; row block 0..l-1 of it
+    // M = E_l^T Q~ with Q~ = H_(1) H_(2) ... H_(m-1), where H_(s) = I - tau_s u_s u_s^T acts on
+    // columns 0..s: the reflectors applied to the l rows of M in that order, a warp per row
     for (int e = tid; e < l * m; e += kRQThreads) {
         const int t = e / m, c = e % m;
         Ms[t * ldw + c] = (t == c) ? 1.0 : 0.0;
@@ -187,11 +206,12 @@ __global__ void __launch_bounds__(kRQThreads) k_block_rq_lq(int m, int l, const 
     for (int s = 1; s <= m - 1; ++s) {
         const double ts = rqt[s];
         if (ts != 0.0) {
+            const double *u = W + (size_t)s * ldw;
             for (int t = warp; t < l; t += nw) {
                 double d = 0.0;
-                for (int c = lane; c <= s; c += 32) d += Ms[t * ldw + c] * (c == s ? 1.0 : W[s * ldw + c]);
+                for (int c = lane; c <= s; c += 32) d = fma(Ms[t * ldw + c], u[c], d);
                 d = warp_sum(d) * ts;
-                for (int c = lane; c <= s; c += 32) Ms[t * ldw + c] -= d * (c == s ? 1.0 : W[s * ldw + c]);
+                for (int c = lane; c <= s; c += 32) Ms[t * ldw + c] = fma(-d, u[c], Ms[t * ldw + c]);
             }
         }
         __syncthreads();
@@ -237,7 +257,7 @@ __global__ void __launch_bounds__(kRQThreads) k_block_rq_lq(int m, int l, const 
     }
 }
 
-size_t block_rq_lq_smem(int m, int l) { return sizeof(double) * ((size_t)(m + l) * (m + 1) + 2 * (size_t)m); }
+size_t block_rq_lq_smem(int m, int l) { return sizeof(double) * ((size_t)(m + l) * (m + kRQPad) + 2 * (size_t)m); }
 
 cudaError_t launch_panel_qr(int m, int b, double *P, int ld, double *V, int ldv, double *tau, cudaStream_t st)
 {

@@ -136,9 +136,14 @@ def test_emu_argument_errors(red):
     work = red.workspace(n, 16)
     assert f(red.ctx, n, 16, A, n, B, n, 0, None, 1, 0, None, 1, EMU, b.hts_params(emu_slices=7), work,
              work.numel()) == b.HTS_ERR_UNSUPPORTED
-    # the digit planes are part of the workspace size; one KiB short is refused
-    need = b.hts_workspace_size(n, 16)
-    assert f(red.ctx, n, 16, A, n, B, n, 0, None, 1, 0, None, 1, EMU, None, work, need - 1024) == \
+    # the digit planes are part of the workspace size; one KiB short is refused (at n = 1024 the
+    # stage-2 layout with its planes is the largest part of the reported size, which also covers
+    # stage 1 and the cuBLAS workspace of its block-reflector products)
+    n2 = 1024
+    A2, B2 = colmajor_empty(n2), colmajor_empty(n2)
+    need = b.hts_workspace_size(n2, 16)
+    work2 = torch.empty(need, dtype=torch.uint8, device="cuda")
+    assert f(red.ctx, n2, 16, A2, n2, B2, n2, 0, None, 1, 0, None, 1, EMU, None, work2, need - 1024) == \
         b.HTS_ERR_WORKSPACE
 
 
