@@ -239,7 +239,7 @@ __device__ __forceinline__ int elim_step(double x, unsigned act, int c, double *
 }
 
 // Bulk of one elimination step: column c of W rows 0 .. rho-2 and of the accumulated column
-// operations G becomes a col_c - b_c col_p, for the active columns c != p (listed in col[0 .. nc-1]).
+// operations G becomes a col_c - b_c col_p, for the active columns c != p (the set bits of cols).
 // G's column c is zero outside the rows of the retired pivots and its diagonal, and every
 // active column's diagonal is the same product D of the earlier steps' a, so only the G rows
 // ret[0 .. ng-1] take part: the retired pivots in order, then p itself, whose diagonal D stands
@@ -247,18 +247,18 @@ __device__ __forceinline__ int elim_step(double x, unsigned act, int c, double *
 // row i, the two half-warps the two columns of a pair, warp bw of the six bulk warps every
 // sixth pair.
 __device__ __forceinline__ void elim_bulk(double *W, double *G, const double *b, double a, double D, int p,
-                                          const int *col, int nc, const int *ret, int ng, int rho, int bw,
-                                          int lane)
+                                          unsigned cols, const int *ret, int ng, int rho, int bw, int lane)
 {
     const int i = lane & 15, h = lane >> 4, nw = rho - 1;
     const bool own = i < nw + ng;
     double *rowp = (i < nw) ? &W[i * kLD] : &G[(own ? ret[i - nw] : 0) * kLD];
     const double vp = own ? ((i == nw + ng - 1) ? D : rowp[p]) : 0.0;
+    const int nc = __popc(cols);
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const int k = 2 * (bw + 6 * e) + h;
         if (own && k < nc) {
-            const int cc = col[k];
+            const int cc = (int)__fns(cols, 0u, k + 1);   // the k-th active column (0-based k)
             rowp[cc] = fma(-b[cc], vp, a * rowp[cc]);
         }
     }
@@ -282,12 +282,9 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
     __shared__ double ps[2];               // {tau applied to the unscaled data, beta}
     __shared__ double vv[kM];              // helper block: current reflector
     __shared__ double eb[2][kM];           // elimination steps: multipliers b (double buffered)
-    __shared__ double ea[2];               // ... a
-    __shared__ double eD[2];               // ... the product of the earlier steps' a
-    __shared__ int ep[2];                  // ... pivot column (-1: the row vanished)
-    __shared__ int ecol[2][kM];            // ... active columns other than the pivot, in order
-    __shared__ int enc[2];                 // ... their number
-    __shared__ int eng[2];                 // ... G rows taking part (retired pivots and p)
+    __shared__ double2 eaD[2];             // ... {a, the product D of the earlier steps' a}
+    __shared__ int4 epc[2];                // ... {pivot column (-1: the row vanished), the other
+                                           //     active columns as a bit mask, G rows taking part}
     __shared__ int eret[kM];               // pivots in the order they were chosen
     __shared__ double zv[kM];              // z, the direction of the opposite reflector
     __shared__ int s_ew[2];                // biased exponent of max |W| (the B block after Q^)
@@ -585,19 +582,11 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
                     // earlier steps' a, the list of the other active columns, the pivot order
                     auto publish = [&](int sl) {
                         if (lane < kM) eb[sl][lane] = b;
-                        if (p >= 0) {
-                            const unsigned cs = act & ~(1u << p);
-                            if (lane < kM && ((cs >> lane) & 1u)) ecol[sl][__popc(cs & ((1u << lane) - 1u))] = lane;
-                        }
                         if (lane == 0) {
-                            ea[sl] = a;
-                            eD[sl] = D;
-                            ep[sl] = p;
-                            if (p >= 0) {
-                                enc[sl] = __popc(act) - 1;
-                                eret[nret] = p;
-                                eng[sl] = nret + 1;
-                            }
+                            // two 16-byte stores carry the step; the bulk finds its columns in the mask
+                            eaD[sl] = make_double2(a, D);
+                            epc[sl] = make_int4(p, p >= 0 ? (int)(act & ~(1u << p)) : 0, nret + 1, 0);
+                            if (p >= 0) eret[nret] = p;
                             if (bad) s_redo = 1;
                         }
                         if (p >= 0) {
@@ -627,10 +616,12 @@ __global__ void __launch_bounds__(kGenThreads, 1) k_s2_chase16(GenArgs a)
                             }
                         } else {
                             // bulk (warps 1 .. 3, 5 .. 7): step t on W rows 0 .. rho-2 and on G
-                            const int pt = ep[cur];
-                            if (pt >= 0)
-                                elim_bulk(W, G, eb[cur], ea[cur], eD[cur], pt, ecol[cur], enc[cur], eret, eng[cur], rho,
+                            const int4 st = epc[cur];
+                            if (st.x >= 0) {
+                                const double2 ad = eaD[cur];
+                                elim_bulk(W, G, eb[cur], ad.x, ad.y, st.x, (unsigned)st.y, eret, st.z, rho,
                                           warp < 4 ? warp - 1 : warp - 2, lane);
+                            }
                         }
                         named_barrier(4, 224);
                     }
