@@ -117,6 +117,25 @@ __device__ void blk_left(double *M, int ld, int r0, int m, int c0, int c1, const
     const double tau = S.tau;
     if (tau == 0.0 || c1 < c0) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (m <= 16) {
+        // short reflectors (stage 2's r <= 16, the ends of stages 0 and 1): g lanes per column,
+        // 32/g columns per warp, so that a column's dot product takes log2(g) shuffle-adds
+        // instead of five (FP64 instructions are the cost on this GPU, whatever their lanes)
+        const int g = m <= 4 ? 4 : (m <= 8 ? 8 : 16);
+        const int per = 32 / g, sub = lane & (g - 1), slot = lane / g;
+        const double v = sub < m ? S.v[sub] : 0.0;
+        for (int cb = c0 + warp * per; cb <= c1; cb += kBW * per) {   // uniform per warp
+            const int c = cb + slot;
+            const bool own = c <= c1 && sub < m;
+            double *col = own ? M + AT(ld, r0, c) : nullptr;
+            const double x = own ? col[sub] : 0.0;
+            double d = x * v;
+            for (int o = 1; o < g; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            d *= tau;
+            if (own) col[sub] = x - d * v;
+        }
+        return;
+    }
     for (int c = c0 + warp; c <= c1; c += kBW) {
         double *col = M + AT(ld, r0, c);
         double d = 0.0;
