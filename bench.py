@@ -708,8 +708,8 @@ def main():
     ap.add_argument("--q", type=int, default=0)
     ap.add_argument("--serial", action="store_true",
                     help="stage 2: each group's delayed updates after its chase (no look-ahead)")
-    ap.add_argument("--tile-m", type=int, default=0, choices=[0, 32, 128],
-                    help="emulated update tiles: 128 lines (tcgen05), 32 (mma.sync), 0 the library's choice")
+    ap.add_argument("--tile-m", type=int, default=0, choices=[0, 32, 64],
+                    help="emulated update tiles: 64 lines (tcgen05), 32 (mma.sync), 0 the library's choice")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="emu mode: also time this many steps with native FP64 updates (0: skip)")

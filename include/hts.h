@@ -70,8 +70,8 @@ typedef enum {
  *             block's RQ runs in shared memory).  Default: min(8, 128/r).
  *  emu_slices number of BF16 digits per FP64 operand in HTS_GEMM_EMU_BF16 mode: 0 or 8 (the
  *             only value this build implements; others give HTS_ERR_UNSUPPORTED).
- *  tile_m     emulated delayed updates of the look-ahead schedule: 0 or 128 selects the
- *             tensor-core kernel on tiles of 128 lines (tcgen05.mma with TMEM accumulators,
+ *  tile_m     emulated delayed updates of the look-ahead schedule: 0 or 64 selects the
+ *             tensor-core kernel on tiles of 64 lines (tcgen05.mma with TMEM accumulators,
  *             the reflector products loaded by TMA; needs r = 16), 32 the warp-level kernel on
  *             tiles of 32 lines (mma.sync); other values give HTS_ERR_UNSUPPORTED.
  *  tile_n     reserved.

@@ -2,13 +2,14 @@
 // tensor cores: tcgen05.mma with the accumulators in tensor memory (TMEM), the reflector
 // products U_k brought into shared memory by the tensor memory accelerator (TMA).
 //
-// A tile is 128 lines (rows of X for the right updates and for Q / Z, columns of X for the left
-// updates), one per TMEM lane.  Per block k, from the last to the first, the lines' window of
+// A tile is 64 lines (rows of X for the right updates and for Q / Z, columns of X for the left
+// updates), each in two MMA rows (TMEM lanes l and l + 64).  Per block k, from the last to
+// the first, the lines' window of
 // w = r + qg - 1 <= 32 positions (r = 16) is multiplied by U_k (w x w, zero padded to 32 x 32)
 // in emulated FP64 (emu_arith.cuh): every line is a fixed-point integer with its own
 // power-of-two unit, split into 8 base-256 digits, and the 36 digit pairs (i, t) with
 // i + t <= 7 are accumulated per level L = i + t in FP32 (exact: every partial sum is an
-// integer below 2^22).  With the 8 digit planes of the lines (A_i, 128 x 32 FP16) and U's 8
+// integer below 2^22).  With the 8 digit planes of the rows (A_i, 128 x 32 FP16) and U's 8
 // transposed digit planes stacked along N (B, 32 x 256 FP16; a digit in [-128, 127] is exact in
 // FP16, and two of them come out of one byte permute and one packed subtraction), one MMA per
 // digit i covers all its levels at once:
@@ -20,17 +21,18 @@
 //
 // The windows of a tile form a chain (consecutive windows overlap), and the chain of the tile
 // on the diagonal is what the next group's chase waits for, so a window's latency is what
-// counts.  A tile is therefore worked by a whole block of 512 threads: thread (h, line) with
-// h = 0..3 holds positions 4h .. 4h+3 and 16+4h .. 16+4h+3 of its line.  The slide by
-// r = 16 positions maps position p of window k to position p + 16 of window k-1, so the
-// overlap stays in the thread that computed it; the four threads of a line (one per group of
-// four warps, all on the line's TMEM lane quarter) exchange only the exponent of the
-// window's largest entry, through shared memory.
+// counts.  A tile is therefore worked by a whole block of 512 threads, eight per line: each
+// line occupies two MMA rows, so that the threads reading its results from TMEM sit on all
+// four lane quarters (all four SM sub-partitions), and the thread with part j = 0..7 holds
+// positions 2j, 2j+1 and 16+2j, 17+2j.  The slide by r = 16 positions maps position p of
+// window k to position p + 16 of window k-1, so the overlap stays in the thread that computed
+// it; the eight threads of a line exchange only the exponent of the window's largest entry,
+// through shared memory.  The MMA computes both rows of a line (the same products).
 //
 // Line activity.  Right updates of A and B: a 32-row subtile s takes blocks kmax .. kT_s + 1
 // here (every reflector of those blocks is still pending for all its rows) and the staircase
 // blocks kT_s .. kstop_s afterwards, reflector by reflector in native FP64 (right_window.cuh),
-// the four subtiles side by side.  Left updates: column c takes blocks from the last one whose
+// the two subtiles side by side.  Left updates: column c takes blocks from the last one whose
 // cut lies left of c down to 0.  A line loads its whole window when it becomes active and
 // stores its whole window after its last block; inactive lines contribute no loads and no
 // stores (their rows of A_i are left as they are and their results are discarded).
@@ -52,14 +54,15 @@ using namespace emu;
 
 namespace {
 
-constexpr int kTcLines = 128;                       // lines per tile (MMA M, TMEM lanes)
-constexpr int kTcSplit = 4;                         // threads per line
-constexpr int kTcThreads = kTcLines * kTcSplit;     // one tile per block
-constexpr int kTcPos = 8;                           // window positions per thread
+constexpr int kTcRows = 128;                        // MMA M, TMEM lanes
+constexpr int kTcLines = 64;                        // lines per tile, each in rows l and l + 64
+constexpr int kTcSplit = 8;                         // threads per line
+constexpr int kTcThreads = kTcLines * kTcSplit;     // one tile per block (4 threads per TMEM lane)
+constexpr int kTcPos = 4;                           // window positions per thread
 constexpr int kWin = 32;                            // window positions (MMA K)
 constexpr int kSlide = 16;                          // r: the window slides by r positions per block
 constexpr int kTmemCols = kDigits * kWin;           // 8 levels x 32 positions
-constexpr int kDigitPlane = kTcLines * kWin * 2;    // one digit plane of the lines: 8 KiB
+constexpr int kDigitPlane = kTcRows * kWin * 2;     // one digit plane of the rows: 8 KiB
 constexpr int kUBytes = kDigits * kWin * kWin * 2;  // U's 8 digit planes: 16 KiB
 constexpr int kStairGroup = 128;                    // threads per 32-row subtile in the staircase
 constexpr int kStairDoubles = 2048;                 // shared scratch per subtile (16 KiB)
@@ -67,11 +70,11 @@ constexpr unsigned kLBO = 128;                      // K-adjacent core matrices
 constexpr unsigned kSBO = 512;                      // row-group-adjacent core matrices
 // instruction descriptor of kind::f16: D FP32 (bit 4), A and B FP16 (type 0 at bits 7 and 10),
 // both K-major, M / 16 at bit 24; N / 8 goes to bit 17
-constexpr unsigned kIdescBase = (1u << 4) | ((unsigned)(kTcLines >> 4) << 24);
+constexpr unsigned kIdescBase = (1u << 4) | ((unsigned)(kTcRows >> 4) << 24);
 constexpr int kWorkerBar = 5;                       // the tile's barrier (1..4: staircase subtiles)
 
 static_assert(kTcSplit * kTcPos == kWin, "a line's positions are split over its threads");
-static_assert((kWin / 2) % kTcSplit == 0, "each thread holds equal parts of both halves");
+static_assert(2 * kTcLines == kTcRows && kTcThreads == 4 * kTcRows, "two rows per line, four threads per row");
 static_assert(4 * kStairDoubles * 8 <= kDigits * kDigitPlane, "staircase scratch fits the digit planes");
 
 struct TcShared {
@@ -85,8 +88,9 @@ struct TcShared {
     int abort;
 };
 
-// Window position of a thread's j-th entry (j = 0..3 in the first half, 4..7 in the second).
-__device__ __forceinline__ int pos_of(int h, int j) { return (j < 4) ? 4 * h + j : kSlide + 4 * h + (j - 4); }
+// Window position of the k-th entry of the thread with part j (j = 0..7): 2j, 2j+1 in the
+// first half, 16+2j, 17+2j in the second, so that the slide by 16 keeps the overlap in-thread.
+__device__ __forceinline__ int pos_of(int j, int k) { return (k < 2) ? 2 * j + k : kSlide + 2 * j + (k - 2); }
 
 // ---- PTX wrappers -------------------------------------------------------------------------
 
@@ -157,27 +161,25 @@ __device__ __forceinline__ void tc_commit(unsigned long long *bar)
                  : "memory");
 }
 
-// The 8 levels of 4 consecutive positions (TMEM columns 32 L + c0 .. 32 L + c0 + 3 of the
+// The 8 levels of 2 consecutive positions (TMEM columns 32 L + c0, 32 L + c0 + 1 of the
 // warp's 32 lanes) in one statement together with the wait for them: tcgen05.ld writes its
 // registers asynchronously, so nothing may read (or move) them before tcgen05.wait::ld, and
 // keeping both in one asm statement leaves the compiler no room to do so.
-__device__ __forceinline__ void tc_ld_levels4(unsigned taddr, unsigned (&v)[kDigits][4])
+__device__ __forceinline__ void tc_ld_levels2(unsigned taddr, unsigned (&v)[kDigits][2])
 {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%32];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%33];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%34];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12, %13, %14, %15}, [%35];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16, %17, %18, %19}, [%36];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%20, %21, %22, %23}, [%37];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%24, %25, %26, %27}, [%38];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%28, %29, %30, %31}, [%39];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%16];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2, %3}, [%17];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4, %5}, [%18];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6, %7}, [%19];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8, %9}, [%20];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10, %11}, [%21];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%12, %13}, [%22];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%14, %15}, [%23];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[0][2]), "=r"(v[0][3]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[1][2]),
-          "=r"(v[1][3]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(v[2][2]), "=r"(v[2][3]), "=r"(v[3][0]), "=r"(v[3][1]),
-          "=r"(v[3][2]), "=r"(v[3][3]), "=r"(v[4][0]), "=r"(v[4][1]), "=r"(v[4][2]), "=r"(v[4][3]), "=r"(v[5][0]),
-          "=r"(v[5][1]), "=r"(v[5][2]), "=r"(v[5][3]), "=r"(v[6][0]), "=r"(v[6][1]), "=r"(v[6][2]), "=r"(v[6][3]),
-          "=r"(v[7][0]), "=r"(v[7][1]), "=r"(v[7][2]), "=r"(v[7][3])
+        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(v[3][0]),
+          "=r"(v[3][1]), "=r"(v[4][0]), "=r"(v[4][1]), "=r"(v[5][0]), "=r"(v[5][1]), "=r"(v[6][0]), "=r"(v[6][1]),
+          "=r"(v[7][0]), "=r"(v[7][1])
         : "r"(taddr), "r"(taddr + kWin), "r"(taddr + 2 * kWin), "r"(taddr + 3 * kWin), "r"(taddr + 4 * kWin),
           "r"(taddr + 5 * kWin), "r"(taddr + 6 * kWin), "r"(taddr + 7 * kWin)
         : "memory");
@@ -213,45 +215,46 @@ __device__ __forceinline__ double *elem(const TcTile &t, int line, int pos)
                          : t.X + (size_t)(line - 1) + (size_t)(pos - 1) * t.ld;
 }
 
-// Loads of a line's window entries: positions pos_of(h, j) < cnt of the window at column
-// (or row) c0, for j = 0 .. jn-1.
-__device__ __forceinline__ void load_part(const TcTile &t, int line, int h, int c0, int cnt, int jn,
+// Loads of a line's window entries: positions pos_of(j, k) < cnt of the window at column (or
+// row) c0, for k = 0 .. kn-1 (the others read as zero).
+__device__ __forceinline__ void load_part(const TcTile &t, int line, int j, int c0, int cnt, int kn,
                                           double (&v)[kTcPos])
 {
 #pragma unroll
-    for (int j = 0; j < kTcPos; ++j) {
-        const int p = pos_of(h, j);
-        v[j] = (j < jn && p < cnt && c0 + p <= t.n) ? *elem(t, line, c0 + p) : 0.0;
+    for (int k = 0; k < kTcPos; ++k) {
+        const int p = pos_of(j, k);
+        v[k] = (k < kn && p < cnt && c0 + p <= t.n) ? *elem(t, line, c0 + p) : 0.0;
     }
 }
 
-// One half of a window's results (half 0: positions 4h .. 4h+3, half 1: 16+4h .. 16+4h+3): the
-// 8 levels read from the accumulator at taddr (the thread's lane quarter, column 0 of the
+// One half of a window's results (half 0: positions 2j, 2j+1, half 1: 16+2j, 17+2j): the 8
+// levels read from the accumulator at taddr (the thread's lane quarter, column 0 of the
 // accumulator), combined into integers in units 2^cu_new.  Positions that leave the window
 // (p >= w - r, or every position in the line's last window) are stored; half 0 keeps the
 // overlap (p < w - r) in carry.  The TMEM read is warp-wide, so every thread takes part.
-__device__ __forceinline__ void epilogue_half(const TcTile &t, int line, int h, unsigned taddr, int half, bool act,
-                                              bool last, int c0, int cu_new, int w, int r, long long (&carry)[4])
+__device__ __forceinline__ void epilogue_half(const TcTile &t, int line, int j, unsigned taddr, int half, bool act,
+                                              bool last, int c0, int cu_new, int w, int r, long long (&carry)[2])
 {
-    unsigned lv[kDigits][4];
-    tc_ld_levels4(taddr + (unsigned)pos_of(h, 4 * half), lv);
+    unsigned lv[kDigits][2];
+    tc_ld_levels2(taddr + (unsigned)pos_of(j, 2 * half), lv);
     if (!act) return;
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-        const int p = pos_of(h, 4 * half + jj);
+    for (int kk = 0; kk < 2; ++kk) {
+        const int p = pos_of(j, 2 * half + kk);
         if (p < w) {
-            const long long v = combine_levels_folded(__uint_as_float(lv[0][jj]), __uint_as_float(lv[1][jj]),
-                                               __uint_as_float(lv[2][jj]), __uint_as_float(lv[3][jj]),
-                                               __uint_as_float(lv[4][jj]), __uint_as_float(lv[5][jj]),
-                                               __uint_as_float(lv[6][jj]), __uint_as_float(lv[7][jj]));
+            const long long v = combine_levels_folded(__uint_as_float(lv[0][kk]), __uint_as_float(lv[1][kk]),
+                                                      __uint_as_float(lv[2][kk]), __uint_as_float(lv[3][kk]),
+                                                      __uint_as_float(lv[4][kk]), __uint_as_float(lv[5][kk]),
+                                                      __uint_as_float(lv[6][kk]), __uint_as_float(lv[7][kk]));
             if ((last || p >= w - r) && c0 + p <= t.n) *elem(t, line, c0 + p) = fixed_to_f64(v, cu_new);
-            if (half == 0) carry[jj] = (p < w - r) ? v : 0;
+            if (half == 0) carry[kk] = (p < w - r) ? v : 0;
         }
     }
 }
 
-// One tile of 128 lines by the block's 512 threads: thread tid works positions pos_of(h, *)
-// of line l0 + m, with h = tid / 128 and m = tid % 128 (its TMEM lane).
+// One tile of 64 lines by the block's 512 threads.  Thread tid (warp w, lane) reads TMEM lane
+// L = 32 (w mod 4) + lane, the MMA row of line l = L mod 64 (rows l and l + 64 both hold that
+// line), and works the positions pos_of(j, *) of the line with j = 2 (w / 4) + L / 64.
 __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, TcPhase &ph, int tid, int *status)
 {
     constexpr int r = kSlide;   // the launcher admits r = 16 only
@@ -261,7 +264,8 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
     const int kmax = nblocks_gen(n, r, j1) - 1;
     const int l0 = tile * kTcLines + 1;
     if (l0 > n || kmax < 0) return;
-    const int h = tid / kTcLines, m = tid % kTcLines, qd = m >> 5;
+    const int qd = (tid >> 5) & 3, L = 32 * qd + (tid & 31);   // lane quarter, TMEM lane
+    const int m = L & (kTcLines - 1), j = 2 * (tid >> 7) + (L >> 6);   // line of the tile, part
     const int lastline = imin(l0 + kTcLines - 1, n);
     const int line = l0 + m;
     const bool lvalid = line <= n;
@@ -276,7 +280,7 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
             const int llast = imin(l0 + 32 * s + 31, n);
             return (llast <= j1) ? -1 : qg + (llast - j1 - 1) / r;
         };
-        klo = kT_of(qd) + 1;   // the line's 32-row subtile is its TMEM lane quarter
+        klo = kT_of(m >> 5) + 1;   // the line's 32-row subtile
         K_lo = kT_of(0) + 1;
     } else if (left) {
         // column c takes the blocks whose cut lies left of it: k <= khi(c), the cut rising with k
@@ -307,12 +311,12 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
             tma_load_3d(S.U[0], t.map, 0, 0, K_hi, &S.bar_u[0]);
         }
         double fresh[kTcPos];
-        long long carry[4] = {0, 0, 0, 0};
+        long long carry[2] = {0, 0};
         int cu = 0;
         if (K_hi <= khi && K_hi >= klo)
-            load_part(t, line, h, j1 + K_hi * r + 1, K_hi == khi ? w : r, K_hi == khi ? kTcPos : 4, fresh);
+            load_part(t, line, j, j1 + K_hi * r + 1, K_hi == khi ? w : r, K_hi == khi ? kTcPos : 2, fresh);
         else
-            load_part(t, line, h, 0, 0, 0, fresh);
+            load_part(t, line, j, 0, 0, 0, fresh);
         // the window whose second half is still in TMEM
         bool p_act = false;
         int p_c0 = 0, p_cu = 0;
@@ -327,35 +331,40 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
             int e = kZeroExp;
             if (act) {
 #pragma unroll
-                for (int j = 0; j < kTcPos; ++j) {
-                    if (pos_of(h, j) < w) {
-                        if (first || j < 4) e = imax(e, exp_of_f64(fresh[j]));
-                        else e = imax(e, exp_of_fixed(carry[j - 4], cu));
+                for (int k = 0; k < kTcPos; ++k) {
+                    if (pos_of(j, k) < w) {
+                        if (first || k < 2) e = imax(e, exp_of_f64(fresh[k]));
+                        else e = imax(e, exp_of_fixed(carry[k - 2], cu));
                     }
                 }
             }
-            S.em[h][m] = e;
+            S.em[j][m] = e;
             group_sync(kWorkerBar, kTcThreads);
-            const int em = imax(imax(S.em[0][m], S.em[1][m]), imax(S.em[2][m], S.em[3][m]));
+            int em = S.em[0][m];
+#pragma unroll
+            for (int q = 1; q < kTcSplit; ++q) em = imax(em, S.em[q][m]);
             const int ua = (em == kZeroExp ? 0 : em + 2) - 64;
             if (act) {
-                // this thread's digits, 4 positions (8 bytes per plane) at a time
+                // this thread's digits, a pair of positions (4 bytes per plane) at a time, into both
+                // rows of the line
+                long long x[kTcPos];
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    long long x[4];
+                for (int k = 0; k < kTcPos; ++k) {
+                    x[k] = 0;
+                    if (pos_of(j, k) < w) x[k] = (first || k < 2) ? f64_to_fixed(fresh[k], ua) : refix(carry[k - 2], cu, ua);
+                }
+                unsigned d01[kDigits], d23[kDigits];
+                digit_pairs_f16(x[0], x[1], d01);
+                digit_pairs_f16(x[2], x[3], d23);
+                const unsigned o0 = kmaj_off(m, pos_of(j, 0)), o1 = kmaj_off(m, pos_of(j, 2));
+                const unsigned o2 = kmaj_off(m + kTcLines, pos_of(j, 0)), o3 = kmaj_off(m + kTcLines, pos_of(j, 2));
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        const int j = 4 * half + jj;
-                        x[jj] = 0;
-                        if (pos_of(h, j) < w) x[jj] = (first || j < 4) ? f64_to_fixed(fresh[j], ua) : refix(carry[jj], cu, ua);
-                    }
-                    unsigned d01[kDigits], d23[kDigits];
-                    digit_pairs_f16(x[0], x[1], d01);
-                    digit_pairs_f16(x[2], x[3], d23);
-                    const unsigned off = kmaj_off(m, pos_of(h, 4 * half));
-#pragma unroll
-                    for (int i = 0; i < kDigits; ++i)
-                        *reinterpret_cast<uint2 *>(S.A + i * kDigitPlane + off) = make_uint2(d01[i], d23[i]);
+                for (int i = 0; i < kDigits; ++i) {
+                    unsigned char *pl = S.A + i * kDigitPlane;
+                    *reinterpret_cast<unsigned *>(pl + o0) = d01[i];
+                    *reinterpret_cast<unsigned *>(pl + o1) = d23[i];
+                    *reinterpret_cast<unsigned *>(pl + o2) = d01[i];
+                    *reinterpret_cast<unsigned *>(pl + o3) = d23[i];
                 }
             }
             fence_async_smem();
@@ -399,10 +408,10 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
             {
                 const int kn = k - 1;
                 if (kn >= K_lo && kn <= khi && kn >= klo)
-                    load_part(t, line, h, j1 + kn * r + 1, kn == khi ? w : r, kn == khi ? kTcPos : 4, fresh);
+                    load_part(t, line, j, j1 + kn * r + 1, kn == khi ? w : r, kn == khi ? kTcPos : 2, fresh);
             }
             // ---- the second half of window k+1 (positions 16 .. w-1 leave it), while the MMAs run
-            if (k < K_hi) epilogue_half(t, line, h, tl + (unsigned)((dbuf ^ 1) * kTmemCols), 1, p_act, true, p_c0, p_cu,
+            if (k < K_hi) epilogue_half(t, line, j, tl + (unsigned)((dbuf ^ 1) * kTmemCols), 1, p_act, true, p_c0, p_cu,
                                         w, r, carry);
             // ---- the first half of window k: the overlap of window k-1 (and position 15)
             if (!mbar_wait(&S.bar_d[dbuf], ph.d[dbuf])) {
@@ -411,7 +420,7 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
             }
             ph.d[dbuf] ^= 1u;
             tc_fence_after();
-            epilogue_half(t, line, h, tl + (unsigned)(dbuf * kTmemCols), 0, act, last, c0, ua + 3, w, r, carry);
+            epilogue_half(t, line, j, tl + (unsigned)(dbuf * kTmemCols), 0, act, last, c0, ua + 3, w, r, carry);
             p_act = act;
             p_c0 = c0;
             p_cu = ua + 3;
@@ -423,7 +432,7 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
         // the second half of the last window
         if (!bad) {
             tc_fence_after();
-            epilogue_half(t, line, h, tl + (unsigned)((dbuf ^ 1) * kTmemCols), 1, p_act, true, p_c0, p_cu, w, r, carry);
+            epilogue_half(t, line, j, tl + (unsigned)((dbuf ^ 1) * kTmemCols), 1, p_act, true, p_c0, p_cu, w, r, carry);
             tc_fence_before();
         }
         if (group_sync_or(kWorkerBar, kTcThreads, bad)) {
@@ -438,12 +447,12 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
         }
     }
 
-    // staircase blocks of the right updates of A and B in native FP64, the 32-row subtiles
-    // side by side (128 threads each; their rows were stored above)
+    // staircase blocks of the right updates of A and B in native FP64, the two 32-row subtiles
+    // side by side (128 threads each, the other 256 threads idle; their rows were stored above)
     if (ab_right) {
         const int s = tid / kStairGroup;
         const int x0 = l0 + 32 * s;
-        if (x0 <= n) {
+        if (s < kTcLines / 32 && x0 <= n) {
             const int llast = imin(x0 + 31, n);
             const int kT = (llast <= j1) ? -1 : qg + (llast - j1 - 1) / r;
             const int skstart = imin(kT, kmax);
@@ -462,7 +471,7 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
 
 // ---------------------------------------------------------------------------------------
 // Persistent look-ahead update launch on the tensor cores (schedule.cuh): one block per SM,
-// taking 128-line tiles in ticket order.
+// taking 64-line tiles in ticket order.
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads, 1) k_s2_update_tc(const __grid_constant__ UpdTcArgs a)
 {

@@ -118,7 +118,7 @@ hts_status check_emu(hts_gemm_mode mode, int r, int q, const hts_params *p)
 {
     if (mode != HTS_GEMM_EMU_BF16) return HTS_OK;
     if (p && p->emu_slices != 0 && p->emu_slices != 8) return HTS_ERR_UNSUPPORTED;
-    if (p && p->tile_m != 0 && p->tile_m != 32 && p->tile_m != 128) return HTS_ERR_UNSUPPORTED;
+    if (p && p->tile_m != 0 && p->tile_m != 32 && p->tile_m != 64) return HTS_ERR_UNSUPPORTED;
     return emu_supported(r, q) ? HTS_OK : HTS_ERR_UNSUPPORTED;
 }
 
@@ -357,7 +357,7 @@ hts_status run_stage2(hts_ctx *ctx, int n, int r, double *A, int lda, double *B,
     const int qzld[2] = {Z ? ldz : ldq, ldq};
     const int qzkind[2] = {Z ? 2 : 3, 3};
     cudaStream_t side = lookahead ? ctx->upd : ctx->side;
-    // the emulated look-ahead updates run on the tcgen05 kernel (128-line tiles) unless the
+    // the emulated look-ahead updates run on the tcgen05 kernel (64-line tiles) unless the
     // mma.sync kernel (32-line tiles) is asked for or the tensor maps cannot be made
     CUtensorMap maps[2 * kSets];
     bool tc = emu && lookahead && tile_m != 32 && update_tc_supported(r, q);

@@ -120,7 +120,7 @@ CASES = [(200, 16, 16), (300, 16, 7), (257, 8, 8), (129, 4, 3), (400, 32, 32), (
          (64, 3, 2), (1000, 16, 16)]
 
 
-@pytest.mark.parametrize("TL", [32, 128])
+@pytest.mark.parametrize("TL", [32, 64, 128])
 @pytest.mark.parametrize("n,r,q", CASES)
 def test_schedule_covers_and_orders(probe, n, r, q, TL):
     groups = list(range(1, n - 1, q))
