@@ -96,9 +96,11 @@ __global__ void __launch_bounds__(128) k_s2_form_u(FormUArgs a)
     __syncwarp();
     if (a.umma) {
         // tcgen05 B operand of block k: the transposed FP16 digit planes U_t^T stacked along N
-        // (N = 32 t + output position, K = input position), K-major core matrices of 8 x 16
-        // bytes, LBO 128 B, SBO 512 B.  Lane = input position; lanes 2i, 2i+1 share a word.
+        // (N = 32 t + output position, K = tc_kidx(input position)), K-major core matrices of
+        // 8 x 16 bytes, LBO 128 B, SBO 512 B.  Lane = input position; lanes 2i, 2i+1 share a word
+        // (tc_kidx keeps them adjacent).
         unsigned char *blk = reinterpret_cast<unsigned char *>((fam ? a.planesZ : a.planesQ) + (size_t)k * kPlaneWords);
+        const int kx = tc_kidx(lane);
         for (int col = 0; col < 32; ++col) {
             unsigned d[kDigits];
             digit_pairs_f16(f64_to_fixed(U[lane * 33 + col], kUnitU), 0, d);   // low halves
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(128) k_s2_form_u(FormUArgs a)
                 const unsigned nb = __shfl_down_sync(0xffffffffu, d[t], 1);
                 if ((lane & 1) == 0) {
                     const int nn = 32 * t + col;
-                    const size_t off = (size_t)(nn >> 3) * 512 + (lane >> 3) * 128 + (nn & 7) * 16 + (lane & 7) * 2;
+                    const size_t off = (size_t)(nn >> 3) * 512 + (kx >> 3) * 128 + (nn & 7) * 16 + (kx & 7) * 2;
                     *reinterpret_cast<unsigned *>(blk + off) = pack_f16(d[t], nb);
                 }
             }

@@ -22,6 +22,12 @@ constexpr int kPlaneWords = kDigits * 2 * 4 * 32;   // uint2 words of one U_k (1
 constexpr int kUnitU = -61;                // U_k entries as integers round(u 2^61)
 constexpr int kZeroExp = -4000;            // "exponent" of a zero value
 
+// Operand K index of window position p (0..31) in the tcgen05 kernel.  A product sums over K,
+// so any order of the positions serves as long as both operands use it; this one puts the
+// positions 2j, 2j+1, 16+2j, 17+2j (the four a thread of that kernel holds) at K = 4j .. 4j+3,
+// next to each other in a core-matrix row, so that a thread writes them with one 8-byte store.
+__host__ __device__ __forceinline__ int tc_kidx(int p) { return 4 * ((p & 15) >> 1) + (p & 1) + 2 * (p >> 4); }
+
 // ---- IEEE-754 double <-> fixed point (integer arithmetic only) --------------------------
 
 // Smallest e with |v| < 2^e, or kZeroExp for zero and subnormal v (treated as zero).

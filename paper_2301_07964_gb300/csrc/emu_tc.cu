@@ -21,13 +21,17 @@
 //
 // The windows of a tile form a chain (consecutive windows overlap), and the chain of the tile
 // on the diagonal is what the next group's chase waits for, so a window's latency is what
-// counts.  A tile is therefore worked by a whole block of 512 threads, eight per line: each
-// line occupies two MMA rows, so that the threads reading its results from TMEM sit on all
-// four lane quarters (all four SM sub-partitions), and the thread with part j = 0..7 holds
-// positions 2j, 2j+1 and 16+2j, 17+2j.  The slide by r = 16 positions maps position p of
-// window k to position p + 16 of window k-1, so the overlap stays in the thread that computed
-// it; the eight threads of a line exchange only the exponent of the window's largest entry,
-// through shared memory.  The MMA computes both rows of a line (the same products).
+// counts.  A tile is therefore worked by a whole block: 512 threads, eight per line, and one
+// more warp whose first thread issues the TMA copies and the MMAs (an MMA issue holds its
+// thread for about as long as the tensor core runs, which would otherwise delay that warp's
+// share of the epilogue).  Each line occupies two MMA rows, so that the threads reading its
+// results from TMEM sit on all four lane quarters (all four SM sub-partitions), and the thread
+// with part j = 0..7 holds positions 2j, 2j+1 and 16+2j, 17+2j, at K = 4j .. 4j+3 of the
+// operands (tc_kidx: one 8-byte store per digit plane and row).  The slide by r = 16 positions
+// maps position p of window k to position p + 16 of window k-1, so the overlap stays in the
+// thread that computed it; the eight threads of a line exchange only the exponent of the
+// window's largest entry, through shared memory.  The MMA computes both rows of a line (the
+// same products).
 //
 // Line activity.  Right updates of A and B: a 32-row subtile s takes blocks kmax .. kT_s + 1
 // here (every reflector of those blocks is still pending for all its rows) and the staircase
@@ -37,10 +41,10 @@
 // stores its whole window after its last block; inactive lines contribute no loads and no
 // stores (their rows of A_i are left as they are and their results are discarded).
 //
-// One block per SM (512 threads at up to 128 registers), all 512 TMEM columns as two
+// One block per SM (544 threads at up to 120 registers), all 512 TMEM columns as two
 // accumulators of 256, so that the MMAs of window k run while the half of window k+1 that
-// leaves the window is combined and stored; thread 0 issues the MMAs and the TMA copies, the
-// next window's U_k is copied while the current one is used.
+// leaves the window is combined and stored; the issuing thread copies the next window's U_k
+// while the current one is used.
 // The blocks take tiles from the look-ahead schedule (schedule.cuh).
 #include <cuda.h>
 
@@ -57,7 +61,9 @@ namespace {
 constexpr int kTcRows = 128;                        // MMA M, TMEM lanes
 constexpr int kTcLines = 64;                        // lines per tile, each in rows l and l + 64
 constexpr int kTcSplit = 8;                         // threads per line
-constexpr int kTcThreads = kTcLines * kTcSplit;     // one tile per block (4 threads per TMEM lane)
+constexpr int kLineThreads = kTcLines * kTcSplit;   // the lines' threads (4 per TMEM lane)
+constexpr int kIssuer = kLineThreads;               // thread of the extra warp that issues TMA and MMA
+constexpr int kTcThreads = kLineThreads + 32;       // one tile per block
 constexpr int kTcPos = 4;                           // window positions per thread
 constexpr int kWin = 32;                            // window positions (MMA K)
 constexpr int kSlide = 16;                          // r: the window slides by r positions per block
@@ -74,7 +80,7 @@ constexpr unsigned kIdescBase = (1u << 4) | ((unsigned)(kTcRows >> 4) << 24);
 constexpr int kWorkerBar = 5;                       // the tile's barrier (1..4: staircase subtiles)
 
 static_assert(kTcSplit * kTcPos == kWin, "a line's positions are split over its threads");
-static_assert(2 * kTcLines == kTcRows && kTcThreads == 4 * kTcRows, "two rows per line, four threads per row");
+static_assert(2 * kTcLines == kTcRows && kLineThreads == 4 * kTcRows, "two rows per line, four threads per row");
 static_assert(4 * kStairDoubles * 8 <= kDigits * kDigitPlane, "staircase scratch fits the digit planes");
 
 struct TcShared {
@@ -264,11 +270,12 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
     const int kmax = nblocks_gen(n, r, j1) - 1;
     const int l0 = tile * kTcLines + 1;
     if (l0 > n || kmax < 0) return;
+    const bool liner = tid < kLineThreads;   // false: the issuing warp
     const int qd = (tid >> 5) & 3, L = 32 * qd + (tid & 31);   // lane quarter, TMEM lane
-    const int m = L & (kTcLines - 1), j = 2 * (tid >> 7) + (L >> 6);   // line of the tile, part
+    const int m = L & (kTcLines - 1), j = liner ? 2 * (tid >> 7) + (L >> 6) : 0;   // line of the tile, part
     const int lastline = imin(l0 + kTcLines - 1, n);
     const int line = l0 + m;
-    const bool lvalid = line <= n;
+    const bool lvalid = liner && line <= n;
     const bool left = t.kind >= 4;
     const bool ab_right = t.kind <= 1;
 
@@ -303,10 +310,10 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
         // The chain from one window to the next is thus first half, exponent, digits, MMA.
         const unsigned tl = tmem + ((unsigned)(32 * qd) << 16);
         int ubuf = 0, dbuf = 0;
-        int u_pend = 0;               // thread 0: buffer with a TMA copy in flight, or -1
+        int u_pend = 0;               // issuer: buffer with a TMA copy in flight, or -1
         unsigned u_par = ph.u[0];     // the phase that copy completes
         bool bad = false;             // this thread met a wait that ran out
-        if (tid == 0) {
+        if (tid == kIssuer) {
             mbar_expect_tx(&S.bar_u[0], kUBytes);
             tma_load_3d(S.U[0], t.map, 0, 0, K_hi, &S.bar_u[0]);
         }
@@ -327,44 +334,42 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
             const bool first = k == khi;
             const bool last = k == klo;
             const int c0 = j1 + k * r + 1;
-            // ---- window k: the unit 2^(ua + 62) above its largest entry, over the line's 4 threads
+            // ---- window k: the unit 2^(ua + 62) above its largest entry, over the line's 8 threads
             int e = kZeroExp;
             if (act) {
 #pragma unroll
-                for (int k = 0; k < kTcPos; ++k) {
-                    if (pos_of(j, k) < w) {
-                        if (first || k < 2) e = imax(e, exp_of_f64(fresh[k]));
-                        else e = imax(e, exp_of_fixed(carry[k - 2], cu));
+                for (int h = 0; h < kTcPos; ++h) {
+                    if (pos_of(j, h) < w) {
+                        if (first || h < 2) e = imax(e, exp_of_f64(fresh[h]));
+                        else e = imax(e, exp_of_fixed(carry[h - 2], cu));
                     }
                 }
             }
-            S.em[j][m] = e;
+            if (liner) S.em[j][m] = e;
             group_sync(kWorkerBar, kTcThreads);
             int em = S.em[0][m];
 #pragma unroll
             for (int q = 1; q < kTcSplit; ++q) em = imax(em, S.em[q][m]);
             const int ua = (em == kZeroExp ? 0 : em + 2) - 64;
             if (act) {
-                // this thread's digits, a pair of positions (4 bytes per plane) at a time, into both
-                // rows of the line
+                // this thread's digits: its four positions sit at K = 4j .. 4j+3 (tc_kidx), one
+                // 8-byte store per plane into each of the line's two rows
                 long long x[kTcPos];
 #pragma unroll
-                for (int k = 0; k < kTcPos; ++k) {
-                    x[k] = 0;
-                    if (pos_of(j, k) < w) x[k] = (first || k < 2) ? f64_to_fixed(fresh[k], ua) : refix(carry[k - 2], cu, ua);
+                for (int h = 0; h < kTcPos; ++h) {
+                    x[h] = 0;
+                    if (pos_of(j, h) < w) x[h] = (first || h < 2) ? f64_to_fixed(fresh[h], ua) : refix(carry[h - 2], cu, ua);
                 }
                 unsigned d01[kDigits], d23[kDigits];
                 digit_pairs_f16(x[0], x[1], d01);
                 digit_pairs_f16(x[2], x[3], d23);
-                const unsigned o0 = kmaj_off(m, pos_of(j, 0)), o1 = kmaj_off(m, pos_of(j, 2));
-                const unsigned o2 = kmaj_off(m + kTcLines, pos_of(j, 0)), o3 = kmaj_off(m + kTcLines, pos_of(j, 2));
+                const unsigned o0 = kmaj_off(m, tc_kidx(pos_of(j, 0)));
+                const unsigned o1 = kmaj_off(m + kTcLines, tc_kidx(pos_of(j, 0)));
 #pragma unroll
                 for (int i = 0; i < kDigits; ++i) {
                     unsigned char *pl = S.A + i * kDigitPlane;
-                    *reinterpret_cast<unsigned *>(pl + o0) = d01[i];
-                    *reinterpret_cast<unsigned *>(pl + o1) = d23[i];
-                    *reinterpret_cast<unsigned *>(pl + o2) = d01[i];
-                    *reinterpret_cast<unsigned *>(pl + o3) = d23[i];
+                    *reinterpret_cast<uint2 *>(pl + o0) = make_uint2(d01[i], d23[i]);
+                    *reinterpret_cast<uint2 *>(pl + o1) = make_uint2(d01[i], d23[i]);
                 }
             }
             fence_async_smem();
@@ -373,7 +378,7 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
                 bad = true;
                 break;
             }
-            if (tid == 0) {
+            if (tid == kIssuer) {
                 tc_fence_after();
                 if (!mbar_wait(&S.bar_u[ubuf], ph.u[ubuf])) {
                     record_error(status, HTS_ERR_TIMEOUT, 0, -2, k, tile);
@@ -404,23 +409,26 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
             }
             ph.u[ubuf] ^= 1u;
             ubuf ^= 1;
-            // the next window's new positions, while the MMAs run (this window's are consumed)
-            {
-                const int kn = k - 1;
-                if (kn >= K_lo && kn <= khi && kn >= klo)
-                    load_part(t, line, j, j1 + kn * r + 1, kn == khi ? w : r, kn == khi ? kTcPos : 2, fresh);
-            }
-            // ---- the second half of window k+1 (positions 16 .. w-1 leave it), while the MMAs run
-            if (k < K_hi) epilogue_half(t, line, j, tl + (unsigned)((dbuf ^ 1) * kTmemCols), 1, p_act, true, p_c0, p_cu,
-                                        w, r, carry);
-            // ---- the first half of window k: the overlap of window k-1 (and position 15)
-            if (!mbar_wait(&S.bar_d[dbuf], ph.d[dbuf])) {
-                record_error(status, HTS_ERR_TIMEOUT, 0, -3, k, tile);
-                bad = true;
+            if (liner) {
+                // the next window's new positions, while the MMAs run (this window's are consumed)
+                {
+                    const int kn = k - 1;
+                    if (kn >= K_lo && kn <= khi && kn >= klo)
+                        load_part(t, line, j, j1 + kn * r + 1, kn == khi ? w : r, kn == khi ? kTcPos : 2, fresh);
+                }
+                // ---- the second half of window k+1 (positions 16 .. w-1 leave it), while the MMAs run
+                if (k < K_hi)
+                    epilogue_half(t, line, j, tl + (unsigned)((dbuf ^ 1) * kTmemCols), 1, p_act, true, p_c0, p_cu, w, r,
+                                  carry);
+                // ---- the first half of window k: the overlap of window k-1 (and position 15)
+                if (!mbar_wait(&S.bar_d[dbuf], ph.d[dbuf])) {
+                    record_error(status, HTS_ERR_TIMEOUT, 0, -3, k, tile);
+                    bad = true;
+                }
+                tc_fence_after();
+                epilogue_half(t, line, j, tl + (unsigned)(dbuf * kTmemCols), 0, act, last, c0, ua + 3, w, r, carry);
             }
             ph.d[dbuf] ^= 1u;
-            tc_fence_after();
-            epilogue_half(t, line, j, tl + (unsigned)(dbuf * kTmemCols), 0, act, last, c0, ua + 3, w, r, carry);
             p_act = act;
             p_c0 = c0;
             p_cu = ua + 3;
@@ -430,7 +438,7 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
             if (k == K_lo) break;
         }
         // the second half of the last window
-        if (!bad) {
+        if (liner && !bad) {
             tc_fence_after();
             epilogue_half(t, line, j, tl + (unsigned)((dbuf ^ 1) * kTmemCols), 1, p_act, true, p_c0, p_cu, w, r, carry);
             tc_fence_before();
@@ -438,7 +446,7 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
         if (group_sync_or(kWorkerBar, kTcThreads, bad)) {
             // stop the tile: let a copy into U that is still in flight land (bounded) before
             // the buffer is reused or the block exits, and the other tiles of the block end
-            if (tid == 0) {
+            if (tid == kIssuer) {
                 if (u_pend >= 0 && !mbar_wait(&S.bar_u[u_pend], u_par)) record_error(status, HTS_ERR_TIMEOUT, 0, -4, 0, tile);
                 *(volatile int *)&S.abort = 1;
             }
@@ -448,7 +456,7 @@ __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, T
     }
 
     // staircase blocks of the right updates of A and B in native FP64, the two 32-row subtiles
-    // side by side (128 threads each, the other 256 threads idle; their rows were stored above)
+    // side by side (128 threads each, the others idle; their rows were stored above)
     if (ab_right) {
         const int s = tid / kStairGroup;
         const int x0 = l0 + 32 * s;
