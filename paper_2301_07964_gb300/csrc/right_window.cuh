@@ -1,12 +1,15 @@
 // Delayed right updates of one tile of rows by the group's reflectors, with a sliding window
 // (Alg. 4, first loop), in native FP64.  Shared by the FP64 apply kernel (stage2.cu) and the
-// emulated one (emu.cu), which runs the staircase blocks of its tiles through it.
+// emulated ones (emu.cu, emu_tc.cu), which run the staircase blocks of their tiles through it.
 //
 // Rows x0 .. x0+NR-1 (NR = NT/4, four lanes per row: lane l of a row owns entries l, l+4, ...
 // of each reflector) receive the reflectors of blocks kstart down to kstop, each block's in
 // sweep order, through a window of w = r + qg - 1 columns in shared memory (sm: w*(NR+1) +
 // qg*r + qg doubles).  kind 0, 1 (A, B): reflector Z^_k^j applies to row x only while
-// x < i4(k, j), the rows the generate phase did not update; kind 2, 3 (Z, Q): all rows.
+// x < i4(k, j), the rows the generate phase did not update; kind 2, 3 (Z, Q): all rows.  A
+// warp none of whose rows takes a reflector skips it (an FP64 instruction costs the same
+// whether one lane or all are active, and in the staircase blocks about half of the pairs of
+// 8-row band and reflector are idle).
 // The next window's new columns are loaded into registers while the current window is updated.
 // tid is the thread's index in its group of NT threads and bar the id of that group's barrier
 // (0 for a whole block).
@@ -66,6 +69,7 @@ __device__ __forceinline__ void right_window_rows(double *X, int ld, int kind, c
             if (tau == 0.0) continue;
             const int jj = j1 + sidx;
             const bool active = x <= n && (kind > 1 || x < j1 + 1 + imax(0, (k + jj - j1 - qg) * r));
+            if (!__any_sync(0xffffffffu, active)) continue;   // the loop is warp-uniform up to here
             const int mlen = imin(r, n - (jj + k * r));
             const double *v = vr + sidx * r;
             double *b = buf + sidx * LDS + rr;
