@@ -309,15 +309,20 @@ def run_ours(args, n, r):
     mode = b.HTS_GEMM_FP64 if args.mode == "fp64" else b.HTS_GEMM_EMU_BF16
     sched_flags = b.HTS_FLAG_SERIAL_UPDATES if args.serial else 0
     red = Reducer(local)
+    tile_m = args.tile_m
+    tile_source = "given on the command line" if tile_m else "the library's default (64-line tcgen05 tiles)"
     if args.q:
         q, q_source = args.q, "given on the command line"
     elif args.tune:
         from paper_2301_07964_gb300 import tune
         path = os.path.join(tempfile.mkdtemp(), "tune.json")
-        q = tune.tuned_q(red, n, r, mode, seed=SEED + 1, cache_path=path, reps=1, retune=True)
-        times = tune.load_cache(path)
-        q_source = "measured by tune.tuned_q on another seeded pencil of this size (ms per call: %s)" % (
-            json.dumps(next(iter(times.values()))["ms"]))
+        tuned = tune.tuned_stage2(red, n, r, mode, seed=SEED + 1, cache_path=path, reps=1, retune=True)
+        q = tuned["q"]
+        if not args.tile_m:
+            tile_m = tuned["tile_m"]
+            tile_source = "measured by tune.tuned_stage2"
+        q_source = "measured by tune.tuned_stage2 on another seeded pencil of this size (ms per call: %s)" % (
+            json.dumps(tuned["ms"]))
     else:
         q, q_source = r, "the library's default q = r (tune.tuned_q measured it fastest at n = 8192, r = 16)"
     A, B = random_rht_pencil(n, r, SEED)
@@ -334,7 +339,7 @@ def run_ours(args, n, r):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, mode=m,
-                   flags=sched_flags, stream=stream, tile_m=args.tile_m)
+                   flags=sched_flags, stream=stream, tile_m=tile_m)
         e1.record(stream)
         return e0, e1
 
@@ -422,7 +427,7 @@ def run_ours(args, n, r):
             dA.t().copy_(hA, non_blocking=True)
             dB.t().copy_(hB, non_blocking=True)
             red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, mode=mode,
-                       flags=sched_flags, stream=stream, tile_m=args.tile_m)
+                       flags=sched_flags, stream=stream, tile_m=tile_m)
             for o, d in zip(outs, (dA, dB, dQ, dZ)):
                 o.copy_(d.t(), non_blocking=True)
             torch.cuda.synchronize()
@@ -494,7 +499,7 @@ def run_ours(args, n, r):
                    "n": n, "r": r, "q": q, "mode": args.mode, "parallelism": "replicas" if ws > 1 else "single",
                    "q_source": q_source,
                    "schedule": "serial" if args.serial else "look-ahead",
-                   "update_tiles": args.tile_m or "library default",
+                   "update_tiles": tile_m or "library default", "update_tiles_source": tile_source,
                    "l2": "inputs (A, B: %.1f GiB) larger than L2" % (2 * 8 * n * n / 2 ** 30)},
         "backward_error": bwd,
         "fp64_updates": fp64_record,
@@ -551,12 +556,20 @@ def run_reduce(args, n, r):
     dA, dB, dQ, dZ = (colmajor_empty(n) for _ in range(4))
     red = Reducer(0)
     stream = torch.cuda.current_stream()
+    mode = b.HTS_GEMM_FP64 if args.mode == "fp64" else b.HTS_GEMM_EMU_BF16
+    p, p_source = args.p, ("given on the command line" if args.p else "the library's default min(8, 128 / r)")
+    if args.tune and not args.p:
+        from paper_2301_07964_gb300 import tune
+        path = os.path.join(tempfile.mkdtemp(), "tune.json")
+        p = tune.tuned_stage1_p(red, n, r, mode, seed=seed + 1, cache_path=path, retune=True)
+        p_source = "measured by tune.tuned_stage1_p on another seeded pencil of this size (ms per call: %s)" % (
+            json.dumps(next(iter(tune.load_cache(path).values()))["ms"]))
 
     def step():
         dA.copy_(dA0)
         dB.copy_(dB0)
-        red.reduce(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=args.q, p=args.p, stream=stream,
-                   mode=b.HTS_GEMM_FP64 if args.mode == "fp64" else b.HTS_GEMM_EMU_BF16)
+        red.reduce(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=args.q, p=p, stream=stream,
+                   mode=mode)
 
     for _ in range(args.warmup):
         step()
@@ -584,7 +597,8 @@ def run_reduce(args, n, r):
         bwd["T_diag_zeros_at_least"] = n // 8
         bwd["T_diag_below_1e-12n"] = int((dT < 1e-12 * n).sum())
     kind = " ill-conditioned B" if args.ill else (" saddle point (n/4 infinite eigenvalues)" if args.saddle else "")
-    print(json.dumps({"workload": "full reduction n=%d r=%d%s, delayed updates %s" % (n, r, kind, args.mode), "p": args.p,
+    print(json.dumps({"workload": "full reduction n=%d r=%d%s, delayed updates %s" % (n, r, kind, args.mode), "p": p,
+                      "p_source": p_source,
                       "ms_per_step": ms, "stage01_ms": s01, "stage2_ms": ms - s01,
                       "gflops_two_stage_21.33n3": 21.33 * n ** 3 / (ms / 1e3) / 1e9,
                       "gflops_stage2_10n3": paper_flops(n) / ((ms - s01) / 1e3) / 1e9,
@@ -655,10 +669,18 @@ def run_batch(args):
         for x, y in zip(dB, B0):
             x.copy_(y)
 
+    params, shape_source = None, "the library's defaults (p = min(8, 64 / r_i), as many blocks per SM as fit)"
+    if args.tune:
+        from paper_2301_07964_gb300 import tune
+        path = os.path.join(tempfile.mkdtemp(), "tune.json")
+        tuned = tune.tuned_batch(red, ns, rs, seed=6, cache_path=path, reps=1, retune=True)
+        params = {"p": tuned["p"], "tile_n": tuned["tile_n"]}
+        shape_source = "measured by tune.tuned_batch on another seeded batch of these sizes (ms per call: %s)" % (
+            json.dumps(tuned["ms"]))
     # the batch is planned once (descriptors and order into the workspace); every step is one
     # planned launch, and the same launch is also timed as a CUDA graph replay
     st = b.hts_plan_batched(red.ctx, ns, rs, dA, ns, dB, ns, b.HTS_COMP_INIT, dQ, ns, b.HTS_COMP_INIT, dZ, ns,
-                            b.HTS_GEMM_FP64, None, work, work.numel(), stream)
+                            b.HTS_GEMM_FP64, params, work, work.numel(), stream)
     assert st == b.HTS_OK, b.status_string(st)
 
     def timed(launch):
@@ -691,7 +713,8 @@ def run_batch(args):
                                   "reduction with Q, Z, one persistent launch (planned once)" % count,
                       "ms_per_batch": ms, "pencils_per_s": count / (ms / 1e3),
                       "gflops_two_stage_21.33n3": flops / (ms / 1e3) / 1e9,
-                      "graph_replay_ms_per_batch": ms_graph, "steps": args.steps}))
+                      "graph_replay_ms_per_batch": ms_graph, "steps": args.steps,
+                      "launch": params or "library defaults", "launch_source": shape_source}))
     red.close()
     return 0
 
@@ -713,7 +736,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="emu mode: also time this many steps with native FP64 updates (0: skip)")
-    ap.add_argument("--tune", action="store_true", help="choose q by tune.tuned_q before timing")
+    ap.add_argument("--tune", action="store_true",
+                    help="measure the launch parameters before timing: q and the update tiles (stage 2), "
+                         "stage 1's p (--workload reduce), p and blocks per SM (--workload batch)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -74,7 +74,10 @@ typedef enum {
  *             tensor-core kernel on tiles of 64 lines (tcgen05.mma with TMEM accumulators,
  *             the reflector products loaded by TMA; needs r = 16), 32 the warp-level kernel on
  *             tiles of 32 lines (mma.sync); other values give HTS_ERR_UNSUPPORTED.
- *  tile_n     reserved.
+ *  tile_n     batched calls: persistent blocks per SM of the launch (0, the default, or more
+ *             than the SM holds: as many as it holds; < 0: HTS_ERR_ARG).  hts_plan_batched keeps
+ *             the value in the context for the planned launches that follow it.  Other calls:
+ *             reserved.
  *  flags      bit 0 (HTS_FLAG_NO_CLEAN): skip the final exact zeroing below the band.
  *             bit 1 (HTS_FLAG_SERIAL_UPDATES): run each group's delayed updates after its
  *             chase instead of beside the next group's chase (the look-ahead of Section
@@ -200,7 +203,8 @@ hts_status hts_reduce(hts_ctx *ctx, int n, int r,
  * of length count (device pointers for the matrices); compq / compz apply to every pencil.
  * Each pencil is reduced by one thread block with its reflectors applied one at a time, so
  * the batch, not a single pencil, supplies the parallelism.  The launch is persistent: as many
- * blocks as the SMs hold at once take pencils from a device queue, largest pencil first.
+ * blocks as the SMs hold at once (or params.tile_n per SM) take pencils from a device queue,
+ * largest pencil first.
  * Limits of this path: n_i <= 512, r_i <= 16 and r_i < n_i (or n_i <= 2),
  * p * r_i <= 64 (p defaults to min(8, 64/r_i)).  `work` (256-byte aligned,
  * hts_workspace_size_batched() bytes) holds the pencil descriptors, the order and the queue.

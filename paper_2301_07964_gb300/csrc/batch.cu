@@ -399,14 +399,16 @@ void batch_stage(void *host, int count, const int *n, const int *r, double *cons
     std::stable_sort(order, order + count, [&](int a, int b2) { return n[a] > n[b2]; });
 }
 
-cudaError_t launch_reduce_batched(void *work, int count, int num_sms, int *status, cudaStream_t st)
+// per_sm: persistent blocks per SM (0 or more than fit: as many as fit).
+cudaError_t launch_reduce_batched(void *work, int count, int num_sms, int per_sm_req, int *status, cudaStream_t st)
 {
-    static int per_sm = 0;
-    if (per_sm == 0) {
+    static int fit = 0;
+    if (fit == 0) {
         int b = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_reduce_batched, kBT, 0) != cudaSuccess || b < 1) b = 1;
-        per_sm = b;
+        fit = b;
     }
+    const int per_sm = (per_sm_req > 0 && per_sm_req < fit) ? per_sm_req : fit;
     unsigned char *w = static_cast<unsigned char *>(work);
     cudaError_t e = cudaMemsetAsync(w + 128, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;

@@ -728,6 +728,7 @@ hts_status check_batched(int count, const int *n, const int *r, double *const *A
     if (mode != HTS_GEMM_FP64 && mode != HTS_GEMM_EMU_BF16) return HTS_ERR_ARG;
     if (mode != HTS_GEMM_FP64) return HTS_ERR_UNSUPPORTED;
     *pp = (p && p->p > 0) ? p->p : 0;
+    if (p && p->tile_n < 0) return HTS_ERR_ARG;
     for (int i = 0; i < count; ++i) {
         if (n[i] < 1 || r[i] < 1 || (n[i] > 2 && r[i] >= n[i])) return HTS_ERR_ARG;
         if (bad_matrix(A[i], lda[i], n[i]) || bad_matrix(B[i], ldb[i], n[i])) return HTS_ERR_ARG;
@@ -766,6 +767,7 @@ hts_status hts_plan_batched(hts_ctx *ctx, int count, const int *n, const int *r,
     if (cudaMemcpyAsync(work, img.data(), img.size(), cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream)) !=
         cudaSuccess)
         return HTS_ERR_CUDA;
+    ctx->batch_per_sm = p ? p->tile_n : 0;
     return HTS_OK;
 }
 
@@ -777,7 +779,8 @@ hts_status hts_reduce_batched_planned(hts_ctx *ctx, int count, void *work, size_
     if (!g.ok) return HTS_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     ProfScope ps(ctx, st);
-    if (launch_reduce_batched(work, count, ctx->num_sms, ctx->d_status, st) != cudaSuccess) return HTS_ERR_CUDA;
+    if (launch_reduce_batched(work, count, ctx->num_sms, ctx->batch_per_sm, ctx->d_status, st) != cudaSuccess)
+        return HTS_ERR_CUDA;
     ps.done(HTS_K_BATCH, 0.0, 0.0);
     return HTS_OK;
 }

@@ -35,6 +35,7 @@ struct hts_ctx {
     cudaEvent_t ev_qz[3];    // serial schedule: set s no longer read by its Q / Z update
     cudaEvent_t ev_upd[3];   // look-ahead: update launch u (u mod 3) finished
     int num_sms;
+    int batch_per_sm;        // blocks per SM of the planned batched launches (0: as many as fit)
     cublasHandle_t blas;     // the WY products of stages 0 and 1 (plain DGEMMs)
 };
 
@@ -346,7 +347,7 @@ size_t batch_work_bytes(int count);
 void batch_stage(void *host, int count, const int *n, const int *r, double *const *A, const int *lda,
                  double *const *B, const int *ldb, double *const *Q, const int *ldq, double *const *Z, const int *ldz,
                  int compq, int compz, int p);
-cudaError_t launch_reduce_batched(void *work, int count, int num_sms, int *status, cudaStream_t st);
+cudaError_t launch_reduce_batched(void *work, int count, int num_sms, int per_sm, int *status, cudaStream_t st);
 int batch_max_n();
 int batch_max_block();
 

@@ -29,7 +29,7 @@ def red():
     r.close()
 
 
-def _run_batch(red, pencils, rs):
+def _run_batch(red, pencils, rs, params=None):
     from paper_2301_07964_gb300.device import colmajor_empty, to_device
     ns = [A.shape[0] for A, _ in pencils]
     dA = [to_device(A) for A, _ in pencils]
@@ -39,7 +39,7 @@ def _run_batch(red, pencils, rs):
     nbytes = b.hts_workspace_size_batched(ns, rs)
     work = torch.empty(max(256, nbytes), dtype=torch.uint8, device="cuda")
     st = b.hts_reduce_batched(red.ctx, ns, rs, dA, ns, dB, ns, b.HTS_COMP_INIT, dQ, ns, b.HTS_COMP_INIT, dZ, ns,
-                              b.HTS_GEMM_FP64, None, work, work.numel())
+                              b.HTS_GEMM_FP64, params, work, work.numel())
     assert st == b.HTS_OK, b.status_string(st)
     dst, info = red.sync_status()
     assert dst == b.HTS_OK, info
@@ -179,3 +179,33 @@ def test_planned_launch_rejects_bad_workspace(red):
     assert b.hts_reduce_batched_planned(red.ctx, 2, work.data_ptr() + 8, need) == b.HTS_ERR_WORKSPACE
     assert b.hts_reduce_batched_planned(red.ctx, 2, work, 64) == b.HTS_ERR_WORKSPACE
     assert b.hts_reduce_batched_planned(red.ctx, 0, work, need) == b.HTS_ERR_ARG
+
+
+def test_launch_shape_and_p(red):
+    """params.tile_n (persistent blocks per SM) changes only which block takes a pencil: the
+    results equal the default launch's bit for bit.  params.p changes stage 1's blocking: the
+    reduction then agrees with the default one in canonical signs (the result is essentially
+    unique once Q e_1 is fixed).  A negative tile_n is an argument error."""
+    from paper_2301_07964_gb300.device import to_host
+    sizes = [40, 64, 100, 130, 200, 17, 96, 250]
+    rs = [max(1, min(8, n // 8)) for n in sizes]
+    pencils = [random_pencil(n, 900 + i) for i, n in enumerate(sizes)]
+    ref = [[to_host(x) for x in mats] for mats in zip(*_run_batch(red, pencils, rs))]
+    for tile_n in (1, 2):
+        got = [[to_host(x) for x in mats] for mats in zip(*_run_batch(red, pencils, rs, {"tile_n": tile_n}))]
+        for i in range(len(sizes)):
+            for g, e, name in zip(got[i], ref[i], "HTQZ"):
+                assert np.array_equal(g, e), (tile_n, sizes[i], name)
+    got = [[to_host(x) for x in mats] for mats in zip(*_run_batch(red, pencils, rs, {"p": 2, "tile_n": 1}))]
+    for i, (n, (A, B)) in enumerate(zip(sizes, pencils)):
+        scale = max(1.0, float(np.abs(A).max()), float(np.abs(B).max()))
+        c_got, c_ref = canonical(*got[i]), canonical(*ref[i])
+        err = max(float(np.abs(x - y).max()) for x, y in zip(c_got, c_ref))
+        assert err <= 1e-12 * n * scale, (n, err)
+    ns, rr = [40, 50], [4, 4]
+    need = b.hts_workspace_size_batched(ns, rr)
+    work = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+    dA = [torch.zeros(40, 40, dtype=torch.float64, device="cuda"), torch.zeros(50, 50, dtype=torch.float64, device="cuda")]
+    st = b.hts_plan_batched(red.ctx, ns, rr, dA, ns, dA, ns, b.HTS_COMP_NONE, None, None, b.HTS_COMP_NONE, None,
+                            None, b.HTS_GEMM_FP64, {"tile_n": -1}, work, work.numel())
+    assert st == b.HTS_ERR_ARG
