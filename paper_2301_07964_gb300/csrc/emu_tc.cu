@@ -258,9 +258,10 @@ __device__ __forceinline__ void epilogue_half(const TcTile &t, int line, int j, 
     }
 }
 
-// One tile of 64 lines by the block's 512 threads.  Thread tid (warp w, lane) reads TMEM lane
-// L = 32 (w mod 4) + lane, the MMA row of line l = L mod 64 (rows l and l + 64 both hold that
-// line), and works the positions pos_of(j, *) of the line with j = 2 (w / 4) + L / 64.
+// One tile of 64 lines by the block's 512 line threads; the issuing warp (tid >= 512) takes no
+// line.  Line thread tid (warp w, lane) reads TMEM lane L = 32 (w mod 4) + lane, the MMA row of
+// line l = L mod 64 (rows l and l + 64 both hold that line), and works the positions
+// pos_of(j, *) of the line with j = 2 (w / 4) + L / 64.
 __device__ void tc_tile(const TcTile &t, int tile, TcShared &S, unsigned tmem, TcPhase &ph, int tid, int *status)
 {
     constexpr int r = kSlide;   // the launcher admits r = 16 only
