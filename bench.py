@@ -627,7 +627,7 @@ def run_probe(args, n, r):
         dA, dB = to_device(A), to_device(B)
         dQ, dZ = colmajor_empty(n), colmajor_empty(n)
         red.stage2(dA, dB, r, dQ, dZ, compq=b.HTS_COMP_INIT, compz=b.HTS_COMP_INIT, q=q, mode=mode,
-                   tile_m=args.tile_m)
+                   flags=b.HTS_FLAG_SERIAL_UPDATES if args.serial else 0, tile_m=args.tile_m)
         st, info = red.sync_status()
         if st != b.HTS_OK:
             raise SystemExit("device error: %s %s" % (b.status_string(st), info))
