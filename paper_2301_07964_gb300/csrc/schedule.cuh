@@ -3,7 +3,7 @@
 //
 // The delayed updates of group g (Alg. 4) run as one persistent launch whose workers take
 // tasks in ticket order, while the chase of group g+1 (Alg. 3) runs beside it.  A task is one
-// tile of TL lines (32 for the mma.sync kernel, 128 for the tcgen05 kernel):
+// tile of TL lines (32 for the mma.sync kernel, 64 for the tcgen05 kernel):
 //   right tile T of A or B   rows TL T+1 .. TL T+TL, every block k the rows still need (the
 //                            windows from the last block to the first, then the staircase);
 //   left tile C of A or B    columns TL C+1 .. TL C+TL, blocks from the lowest one whose cut lies
