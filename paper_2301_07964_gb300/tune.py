@@ -67,6 +67,12 @@ def batch_shape_candidates() -> list:
     return [0, 1, 2]
 
 
+def default_then_largest(values):
+    """Tie preference for p: 0 (the library's per-pencil default) first, else the largest."""
+    values = list(values)
+    return 0 if 0 in values else max(values)
+
+
 def coordinate_search(run: Callable[[dict], float], start: dict, axes: list, reps: int = 2,
                       warmup: int = 1, tie: float = 0.01):
     """Minimise run(config) one parameter at a time.  axes: (name, candidates, prefer) in the
@@ -261,7 +267,7 @@ def tuned_batch(red, ns: list, rs: list, seed: int = 0, cache_path: Optional[str
         return _timer(red, stream, call, "batched reduction while tuning %s" % cfg)
 
     best, seen = coordinate_search(run, {"p": 0, "tile_n": 0},
-                                   [("tile_n", batch_shape_candidates(), min), ("p", pc, lambda ks: max(ks, key=lambda v: (v == 0, v)))],
+                                   [("tile_n", batch_shape_candidates(), min), ("p", pc, default_then_largest)],
                                    reps=reps)
     choice = {"p": int(best["p"]), "tile_n": int(best["tile_n"])}
     store_cache(path, key, choice, seen)

@@ -92,3 +92,9 @@ def test_cache_of_a_parameter_set(tmp_path):
     tune.store_cache(path, "k", {"q": 16, "tile_m": 64}, {(("q", 16), ("tile_m", 64)): 3.0, (("q", 8), ("tile_m", 0)): 5.0})
     data = json.load(open(path))
     assert data["k"] == {"q": 16, "tile_m": 64, "ms": {"q=16,tile_m=64": 3.0, "q=8,tile_m=0": 5.0}}
+
+
+def test_default_then_largest():
+    assert tune.default_then_largest([2, 4, 0, 8]) == 0
+    assert tune.default_then_largest([2, 8, 4]) == 8
+    assert tune.choose({0: 8.54, 2: 10.4, 4: 9.06, 8: 8.53}, prefer=tune.default_then_largest) == 0
